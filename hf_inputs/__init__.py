@@ -1,0 +1,4 @@
+"""Seeded synthetic inputs (meshes, parameters, seed states) shared by the
+oracle, the tests and the bench.  Holds none of the method's arithmetic."""
+from .mesh import (Mesh, square_p2, cube_p2, pressure_nodes, seed_faces, seed_state,
+                   batch_instances, round_even, TRI_EDGES, TET_EDGES)
