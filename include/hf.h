@@ -1,0 +1,211 @@
+/*
+ * hf.h - C ABI of the GB300 hydraulic-fracture Newton step.
+ *
+ * The library advances the fully-coupled hydro-mechanical system of
+ * Giovanardi, Serebrinsky & Radovitzky, "A fully-coupled computational
+ * framework for large-scale simulation of fluid-driven fracture propagation on
+ * parallel computers" (arXiv 1911.10275):
+ *   - linear elasticity on discontinuous P2 elements (Sec. 3, Eq.
+ *     weakElastoStatics), with IIPG-type DG consistency + stability terms on
+ *     intact interior facets;
+ *   - a linear-decreasing cohesive law on activated facets (Eq. tsl);
+ *   - continuous P2 lubrication flow, cubic law q = -w^3/(12 mu) grad p, on
+ *     fluid-filled facets (Eq. lubrication, Eq. weakPressure), backward Euler
+ *     in time (Eq. discreteElastoStatics, Eq. discreteLubrication);
+ *   - one Newton iteration per hf_newton_step: assembly of the residual and of
+ *     the Jacobian blocks [A B; C D] (Eq. fully-coupled-fully-discrete) into a
+ *     fixed-pattern element-block CSR, then ILU(0) block-Jacobi preconditioned
+ *     GMRES (FP64, or FP32 inner solves inside FP64 iterative refinement).
+ *
+ * Conventions shared with every caller:
+ *   - 2D: 6-node triangles, vertices 0,1,2 counter-clockwise, mid-nodes
+ *     3=(0,1), 4=(1,2), 5=(2,0).  Plane strain.
+ *   - 3D: 10-node tetrahedra with positive volume, vertices 0..3, mid-nodes
+ *     4=(0,1), 5=(1,2), 6=(0,2), 7=(0,3), 8=(1,3), 9=(2,3).
+ *   - Local facet i of an element is the facet opposite vertex i.  Its
+ *     face-node order is: its vertices in ascending local index, then the
+ *     mid-nodes of its edges in ascending local index (3 nodes in 2D, 6 in 3D).
+ *   - face_elems[2f] = e_minus, face_elems[2f+1] = e_plus (-1: boundary).  The
+ *     jump is [[u]] = u(e_plus) - u(e_minus); the facet normal n is the outward
+ *     normal of e_minus (Eq. displacementJump); the opening is w = [[u]].n.
+ *   - Facet quadrature points are generated in e_minus's face-vertex order
+ *     (collapsed-coordinate Gauss rules, 5 points per direction).
+ *   - Displacement unknown (element e, local node a, component k) has index
+ *     e*nen*dim + a*dim + k in every host array of this API.
+ *   - Pressure unknowns live on every node of a crackable facet; pressure DOF
+ *     j is the j-th smallest such global node id.
+ *
+ * Error behaviour: every call returns an hf_status; nothing throws or exits.
+ * A failed call leaves the state as it was unless it returns HF_ERR_CUDA, in
+ * which case the handle is poisoned and later calls return HF_ERR_STATE.
+ * hf_last_error() describes the last failure.  One handle = one CUDA stream;
+ * a handle is not thread-safe.  Host arrays passed in are copied; output
+ * arrays are caller-allocated with the sizes stated.
+ */
+#ifndef HF_H
+#define HF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int hf_status;
+enum {
+  HF_OK = 0,
+  HF_ERR_INVALID_ARG = -1,
+  HF_ERR_OOM = -2,
+  HF_ERR_CUDA = -3,
+  HF_ERR_NOT_CONVERGED = -4,
+  HF_ERR_NONFINITE = -5,
+  HF_ERR_TIMEOUT = -6,
+  HF_ERR_DEVICE_ASSERT = -7,
+  HF_ERR_STATE = -8
+};
+
+typedef struct hf_mesh hf_mesh; /* opaque; owns all device memory */
+
+/* Mesh, interface list and boundary data (Sec. 3: partition of the domain,
+ * interior boundary, every interior facet carries an interface element).
+ * All arrays are host memory owned by the caller and copied at create. */
+typedef struct {
+  int dim;                        /* 2 or 3 */
+  int order;                      /* polynomial order; must be 2 */
+  int64_t n_nodes;
+  const double* xyz;              /* n_nodes*dim */
+  int64_t n_elems;
+  const int32_t* elem_nodes;      /* n_elems*(6|10), node order above */
+  int64_t n_faces;                /* all facets, interior and boundary */
+  const int32_t* face_elems;      /* n_faces*2: e_minus, e_plus (-1 boundary) */
+  const int8_t* face_local;       /* n_faces*2: local facet ids (-1 boundary) */
+  const int8_t* face_crackable;   /* n_faces: 1 = may become cohesive/fluid */
+  int64_t n_dirichlet;
+  const int64_t* dir_dof;         /* displacement unknowns held fixed */
+  const double* dir_val;          /* their values (strong, nodal) */
+  int64_t n_neumann;
+  const int32_t* neu_face;        /* boundary facets carrying a traction */
+  const double* neu_traction;     /* n_neumann*dim, constant per facet */
+} hf_mesh_desc;
+
+/* Solver options.  Defaults come from hf_default_solver_opts. */
+enum { HF_PREC_FP64 = 0, HF_PREC_MIXED = 1 };
+typedef struct {
+  int precision;        /* HF_PREC_FP64 or HF_PREC_MIXED (FP32 SpMV/ILU in FP64 IR) */
+  int restart;          /* GMRES restart length m (1..30) */
+  int max_iters;        /* cap on GMRES iterations per Newton step (all cycles) */
+  double rtol;          /* GMRES: ||J d + R|| <= rtol ||R|| */
+  double inner_rtol;    /* mixed: reduction asked of each FP32 inner solve */
+  int jacobi_block;     /* elements per block-Jacobi subdomain (>= 1) */
+  int fluid_scaling;    /* 1: scale pressure rows by c^n (remark in Sec. 3) */
+  double newton_tol;    /* relative-increment tolerance of hf_newton_step */
+  int use_graphs;       /* 1: capture each GMRES cycle in a CUDA graph */
+} hf_solver_opts;
+
+/* Report of one Newton iteration (Sec. 3: convergence on the Euclidean norms
+ * of the relative increments of both nodal arrays). */
+typedef struct {
+  double du_rel;        /* ||dU||_2 / ||U||_2 after the update */
+  double dp_rel;        /* ||dP||_2 / ||P||_2 after the update */
+  double res_norm;      /* ||R||_2 at the start of the iteration */
+  double lin_res;       /* ||J d + R||_2 / ||R||_2 reached by GMRES */
+  int gmres_iters;      /* inner (Arnoldi) iterations taken */
+  int refinements;      /* mixed mode: outer refinement steps */
+  int converged;        /* du_rel <= tol && dp_rel <= tol */
+  int lin_converged;    /* lin_res <= rtol */
+} hf_newton_report;
+
+void hf_default_solver_opts(hf_solver_opts* o);
+
+/* Builds the fixed-topology discretisation: facet geometry, pressure DOF map,
+ * element-block pattern, block-Jacobi subdomains and their level schedule.
+ * cuda_stream: a cudaStream_t (NULL = a new stream owned by the handle).
+ * Errors: HF_ERR_INVALID_ARG on malformed input (bad ids, dim/order, a facet
+ * whose elements do not share it), HF_ERR_OOM, HF_ERR_CUDA. */
+hf_status hf_mesh_create(const hf_mesh_desc* desc, void* cuda_stream, hf_mesh** out);
+hf_status hf_mesh_destroy(hf_mesh* h);
+
+/* Elastic and cohesive material (Sec. 2, Eq. tsl; stability b of Eq.
+ * weakElastoStatics).  Rebuilds the cached linear blocks (bulk B^T D B and
+ * the intact-facet DG blocks).  E > 0, -1 < nu < 0.5, sigma_c > 0,
+ * delta_c > 0, b_stab > 0. */
+hf_status hf_set_material(hf_mesh* h, double E, double nu, double sigma_c, double delta_c,
+                          double b_stab);
+
+/* Fluid and injection (Eq. lubrication, Eq. discreteLubrication): viscosity mu,
+ * total injection rate Q0 split over n_inj pressure DOFs with the given
+ * weights (a point source: one DOF, weight 1), fluid-activation opening
+ * delta_f, time step dt, vapour pressure p_v, pressure cut-off switch, and the
+ * length L of the fluid-row scaling c^n = 12 mu (L / max w^n)^3. */
+hf_status hf_set_injection(hf_mesh* h, double mu, double Q0, int64_t n_inj,
+                           const int64_t* p_dofs, const double* weights, double delta_f,
+                           double dt, double p_vapor, int cutoff_on, double L_ref);
+
+hf_status hf_set_solver(hf_mesh* h, const hf_solver_opts* o);
+
+/* State (U, P, alpha, beta, w^n, t).  U: n_elems*nen*dim, P: n_p,
+ * alpha/beta: n_faces, w_old: n_faces*nfn face-node openings at t^n (NULL:
+ * take the opening of U).  Rescales the fluid rows from w_old. */
+hf_status hf_set_state(hf_mesh* h, const double* U, const double* P, const int8_t* alpha,
+                       const int8_t* beta, const double* w_old, double t);
+hf_status hf_get_state(hf_mesh* h, double* U, double* P, int8_t* alpha, int8_t* beta,
+                       double* w_old, double* t);
+
+/* One Newton iteration of Sec. 3 (assemble R and J, solve J d = -R, update).
+ * Returns HF_OK even if the iteration did not converge (see rep->converged);
+ * HF_ERR_NONFINITE if a norm is not finite (state then unchanged). */
+hf_status hf_newton_step(hf_mesh* h, hf_newton_report* rep);
+
+/* Fracture criterion (Sec. 3, activation of the TSL): on crackable intact
+ * facets, alpha := 1 where the normal DG traction n.<sigma>n + (b/h)(lambda +
+ * 2 mu) w exceeds sigma_c at a facet quadrature point.  Irreversible.
+ * n_new_alpha: number of facets switched. */
+hf_status hf_check_fracture_criterion(hf_mesh* h, int64_t* n_new_alpha);
+
+/* End of a time step (Sec. 3: beta lagged to the end of the step; Remark on
+ * delta_f): beta := 1 on cohesive facets whose opening exceeds delta_f at a
+ * quadrature point, w^n := w^{n+1}, t += dt, c^n recomputed. */
+hf_status hf_accept_step(hf_mesh* h, int64_t* n_new_beta);
+
+/* Openings at the face nodes of every facet (n_faces*nfn, 0 on boundary
+ * facets), pressures (n_p), alpha, beta (n_faces).  Any pointer may be NULL. */
+hf_status hf_get_opening_pressure(hf_mesh* h, double* w_face_nodes, double* p, int8_t* alpha,
+                                  int8_t* beta);
+
+/* Sizes fixed by the mesh. */
+hf_status hf_get_sizes(const hf_mesh* h, int64_t* n_u, int64_t* n_p, int64_t* nfn);
+
+/* Diagnostics used by the parity tests: residual R at the current state
+ * (n_u + n_p, host layout), and y = J x for a host vector x (same layout).
+ * Both include the row scaling and the identity rows of the Newton system. */
+hf_status hf_eval_residual(hf_mesh* h, double* R);
+hf_status hf_apply_jacobian(hf_mesh* h, const double* x, double* y);
+/* Largest normal DG traction over the quadrature points of each crackable
+ * intact facet (-inf elsewhere), as tested by hf_check_fracture_criterion. */
+hf_status hf_get_criterion_traction(hf_mesh* h, double* tmax);
+/* z = M^-1 x with the block-Jacobi ILU(0) preconditioner of the current state. */
+hf_status hf_apply_preconditioner(hf_mesh* h, const double* x, double* z);
+/* Solve J d = rhs with the configured GMRES (no state change); host vectors. */
+hf_status hf_solve_linear(hf_mesh* h, const double* rhs, double* d, hf_newton_report* rep);
+
+/* Profiling: with on != 0, every kernel class of the Newton step is bracketed
+ * by CUDA events on the handle's stream (GMRES cycles are then launched
+ * without graphs).  hf_get_kernel_times returns the accumulated milliseconds
+ * and launch counts since profiling was switched on, per class:
+ * 0 SpMV (Krylov precision), 1 preconditioner apply, 2 Gram-Schmidt + norm,
+ * 3 ILU factorisation, 4 assembly (facet terms + residual), 5 FP64 SpMV of the
+ * refinement residual, 6 Newton update, 7 unused.  ms and launches hold 8. */
+hf_status hf_set_profiling(hf_mesh* h, int on);
+hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
+/* Structure counts: [0] elements, [1] interior facet slots (element-side pairs
+ * with a neighbour), [2] slots inside block-Jacobi subdomains, [3] deepest
+ * level schedule, [4] subdomains, [5] nonlinear facets, [6] pressure
+ * unknowns, [7] facets.  st holds 8. */
+hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
+
+const char* hf_last_error(const hf_mesh* h);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HF_H */

@@ -1,0 +1,277 @@
+"""ctypes binding of include/hf.h.  Argument marshalling only: every step of
+the Newton iteration runs in the CUDA library.  Importing fails loudly if the
+shared library cannot be built or loaded; there is no CPU fallback."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+from . import build as _build
+
+HF_OK = 0
+HF_PREC_FP64 = 0
+HF_PREC_MIXED = 1
+STATUS = {0: "HF_OK", -1: "HF_ERR_INVALID_ARG", -2: "HF_ERR_OOM", -3: "HF_ERR_CUDA",
+          -4: "HF_ERR_NOT_CONVERGED", -5: "HF_ERR_NONFINITE", -6: "HF_ERR_TIMEOUT",
+          -7: "HF_ERR_DEVICE_ASSERT", -8: "HF_ERR_STATE"}
+
+_dp = C.POINTER(C.c_double)
+_i32p = C.POINTER(C.c_int32)
+_i64p = C.POINTER(C.c_int64)
+_i8p = C.POINTER(C.c_int8)
+
+
+class hf_mesh_desc(C.Structure):
+    _fields_ = [("dim", C.c_int), ("order", C.c_int), ("n_nodes", C.c_int64), ("xyz", _dp),
+                ("n_elems", C.c_int64), ("elem_nodes", _i32p), ("n_faces", C.c_int64),
+                ("face_elems", _i32p), ("face_local", _i8p), ("face_crackable", _i8p),
+                ("n_dirichlet", C.c_int64), ("dir_dof", _i64p), ("dir_val", _dp),
+                ("n_neumann", C.c_int64), ("neu_face", _i32p), ("neu_traction", _dp)]
+
+
+class hf_solver_opts(C.Structure):
+    _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int),
+                ("rtol", C.c_double), ("inner_rtol", C.c_double), ("jacobi_block", C.c_int),
+                ("fluid_scaling", C.c_int), ("newton_tol", C.c_double), ("use_graphs", C.c_int)]
+
+
+class hf_newton_report(C.Structure):
+    _fields_ = [("du_rel", C.c_double), ("dp_rel", C.c_double), ("res_norm", C.c_double),
+                ("lin_res", C.c_double), ("gmres_iters", C.c_int), ("refinements", C.c_int),
+                ("converged", C.c_int), ("lin_converged", C.c_int)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+_H = C.c_void_p
+SIGNATURES = {
+    "hf_default_solver_opts": (None, [C.POINTER(hf_solver_opts)]),
+    "hf_mesh_create": (C.c_int, [C.POINTER(hf_mesh_desc), C.c_void_p, C.POINTER(C.c_void_p)]),
+    "hf_mesh_destroy": (C.c_int, [_H]),
+    "hf_set_material": (C.c_int, [_H, C.c_double, C.c_double, C.c_double, C.c_double, C.c_double]),
+    "hf_set_injection": (C.c_int, [_H, C.c_double, C.c_double, C.c_int64, _i64p, _dp, C.c_double,
+                                   C.c_double, C.c_double, C.c_int, C.c_double]),
+    "hf_set_solver": (C.c_int, [_H, C.POINTER(hf_solver_opts)]),
+    "hf_set_state": (C.c_int, [_H, _dp, _dp, _i8p, _i8p, _dp, C.c_double]),
+    "hf_get_state": (C.c_int, [_H, _dp, _dp, _i8p, _i8p, _dp, _dp]),
+    "hf_newton_step": (C.c_int, [_H, C.POINTER(hf_newton_report)]),
+    "hf_check_fracture_criterion": (C.c_int, [_H, _i64p]),
+    "hf_accept_step": (C.c_int, [_H, _i64p]),
+    "hf_get_opening_pressure": (C.c_int, [_H, _dp, _dp, _i8p, _i8p]),
+    "hf_get_sizes": (C.c_int, [_H, _i64p, _i64p, _i64p]),
+    "hf_eval_residual": (C.c_int, [_H, _dp]),
+    "hf_apply_jacobian": (C.c_int, [_H, _dp, _dp]),
+    "hf_get_criterion_traction": (C.c_int, [_H, _dp]),
+    "hf_apply_preconditioner": (C.c_int, [_H, _dp, _dp]),
+    "hf_solve_linear": (C.c_int, [_H, _dp, _dp, C.POINTER(hf_newton_report)]),
+    "hf_set_profiling": (C.c_int, [_H, C.c_int]),
+    "hf_get_kernel_times": (C.c_int, [_H, _dp, _i64p]),
+    "hf_get_stats": (C.c_int, [_H, _i64p]),
+    "hf_last_error": (C.c_char_p, [_H]),
+}
+KERNEL_CLASSES = ["spmv", "precond", "orth", "factor", "assembly", "spmv64", "update", "unused"]
+
+_lib = None
+
+
+def load(build_if_missing: bool = True):
+    """Load libhfgb300.so (building it in-tree first when absent)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if not build_if_missing:
+            raise ImportError(f"{path} is missing; run __graft_entry__.build()")
+        _build.build()
+    lib = C.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(a, ct):
+    return None if a is None else a.ctypes.data_as(C.POINTER(ct))
+
+
+class HFError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class HFMesh:
+    """One discretised problem on the GPU (an hf_mesh handle)."""
+
+    def __init__(self, dim, xyz, elem_nodes, face_elems, face_local, face_crackable, dir_dof, dir_val,
+                 neu_face=None, neu_traction=None, stream=None):
+        self.lib = load()
+        self._keep = [np.ascontiguousarray(xyz, dtype=np.float64),
+                      np.ascontiguousarray(elem_nodes, dtype=np.int32),
+                      np.ascontiguousarray(face_elems, dtype=np.int32),
+                      np.ascontiguousarray(face_local, dtype=np.int8),
+                      np.ascontiguousarray(face_crackable, dtype=np.int8),
+                      np.ascontiguousarray(dir_dof, dtype=np.int64),
+                      np.ascontiguousarray(dir_val, dtype=np.float64),
+                      np.ascontiguousarray(neu_face if neu_face is not None else np.zeros(0), dtype=np.int32),
+                      np.ascontiguousarray(neu_traction if neu_traction is not None else np.zeros(0),
+                                           dtype=np.float64)]
+        x, en, fe, fl, fc, dd, dv, nf_, nt = self._keep
+        d = hf_mesh_desc(dim, 2, x.shape[0], _ptr(x, C.c_double), en.shape[0], _ptr(en, C.c_int32),
+                         fe.shape[0], _ptr(fe, C.c_int32), _ptr(fl, C.c_int8), _ptr(fc, C.c_int8),
+                         dd.shape[0], _ptr(dd, C.c_int64), _ptr(dv, C.c_double),
+                         nf_.shape[0], _ptr(nf_, C.c_int32), _ptr(nt, C.c_double))
+        h = C.c_void_p()
+        st = self.lib.hf_mesh_create(C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h))
+        if st != HF_OK:
+            raise HFError(st, "hf_mesh_create failed")
+        self.h = h
+        self.dim = dim
+        self.n_faces = fe.shape[0]
+        nu, np_, nfn = C.c_int64(), C.c_int64(), C.c_int64()
+        self._check(self.lib.hf_get_sizes(h, C.byref(nu), C.byref(np_), C.byref(nfn)))
+        self.n_u, self.n_p, self.nfn = nu.value, np_.value, nfn.value
+        self.N = self.n_u + self.n_p
+
+    @classmethod
+    def from_mesh(cls, m, **kw):
+        return cls(m.dim, m.xyz, m.elem_nodes, m.face_elems, m.face_local, m.face_crackable,
+                   m.dir_dof, m.dir_val, **kw)
+
+    def _check(self, st):
+        if st != HF_OK:
+            raise HFError(st, self.lib.hf_last_error(self.h).decode())
+        return st
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hf_mesh_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- set-up
+    def hf_set_material(self, E, nu, sigma_c, delta_c, b_stab=10.0):
+        self._check(self.lib.hf_set_material(self.h, E, nu, sigma_c, delta_c, b_stab))
+
+    def hf_set_injection(self, mu, Q0, p_dofs, weights, delta_f, dt, p_vapor=0.0, cutoff_on=False, L_ref=1.0):
+        pd = np.ascontiguousarray(p_dofs, dtype=np.int64)
+        w = np.ascontiguousarray(weights, dtype=np.float64)
+        self._check(self.lib.hf_set_injection(self.h, mu, Q0, pd.shape[0], _ptr(pd, C.c_int64),
+                                              _ptr(w, C.c_double), delta_f, dt, p_vapor,
+                                              int(bool(cutoff_on)), L_ref))
+
+    def default_opts(self):
+        o = hf_solver_opts()
+        self.lib.hf_default_solver_opts(C.byref(o))
+        return o
+
+    def hf_set_solver(self, **kw):
+        o = self.default_opts()
+        for k, v in kw.items():
+            if k == "precision" and isinstance(v, str):
+                v = HF_PREC_MIXED if v == "mixed" else HF_PREC_FP64
+            setattr(o, k, v)
+        self._check(self.lib.hf_set_solver(self.h, C.byref(o)))
+        return o
+
+    def hf_set_state(self, U, P, alpha, beta, w_old=None, t=0.0):
+        U = np.ascontiguousarray(U, dtype=np.float64)
+        P = np.ascontiguousarray(P, dtype=np.float64)
+        a = np.ascontiguousarray(alpha, dtype=np.int8)
+        b = np.ascontiguousarray(beta, dtype=np.int8)
+        wo = None if w_old is None else np.ascontiguousarray(w_old, dtype=np.float64)
+        self._check(self.lib.hf_set_state(self.h, _ptr(U, C.c_double), _ptr(P, C.c_double), _ptr(a, C.c_int8),
+                                          _ptr(b, C.c_int8), _ptr(wo, C.c_double), float(t)))
+
+    def hf_get_state(self):
+        U = np.zeros(self.n_u)
+        P = np.zeros(max(self.n_p, 1))
+        a = np.zeros(self.n_faces, np.int8)
+        b = np.zeros(self.n_faces, np.int8)
+        wo = np.zeros(self.n_faces * self.nfn)
+        t = C.c_double()
+        self._check(self.lib.hf_get_state(self.h, _ptr(U, C.c_double), _ptr(P, C.c_double), _ptr(a, C.c_int8),
+                                          _ptr(b, C.c_int8), _ptr(wo, C.c_double), C.byref(t)))
+        return U, P[: self.n_p], a, b, wo.reshape(self.n_faces, self.nfn), t.value
+
+    # -- the Newton step and its companions
+    def hf_newton_step(self):
+        r = hf_newton_report()
+        self._check(self.lib.hf_newton_step(self.h, C.byref(r)))
+        return r.as_dict()
+
+    def hf_check_fracture_criterion(self):
+        n = C.c_int64()
+        self._check(self.lib.hf_check_fracture_criterion(self.h, C.byref(n)))
+        return n.value
+
+    def hf_accept_step(self):
+        n = C.c_int64()
+        self._check(self.lib.hf_accept_step(self.h, C.byref(n)))
+        return n.value
+
+    def hf_get_opening_pressure(self):
+        w = np.zeros(self.n_faces * self.nfn)
+        p = np.zeros(max(self.n_p, 1))
+        a = np.zeros(self.n_faces, np.int8)
+        b = np.zeros(self.n_faces, np.int8)
+        self._check(self.lib.hf_get_opening_pressure(self.h, _ptr(w, C.c_double), _ptr(p, C.c_double),
+                                                     _ptr(a, C.c_int8), _ptr(b, C.c_int8)))
+        return w.reshape(self.n_faces, self.nfn), p[: self.n_p], a, b
+
+    # -- diagnostics
+    def hf_eval_residual(self):
+        R = np.zeros(self.N)
+        self._check(self.lib.hf_eval_residual(self.h, _ptr(R, C.c_double)))
+        return R
+
+    def hf_apply_jacobian(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros(self.N)
+        self._check(self.lib.hf_apply_jacobian(self.h, _ptr(x, C.c_double), _ptr(y, C.c_double)))
+        return y
+
+    def hf_get_criterion_traction(self):
+        t = np.zeros(self.n_faces)
+        self._check(self.lib.hf_get_criterion_traction(self.h, _ptr(t, C.c_double)))
+        return t
+
+    def hf_apply_preconditioner(self, x):
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        z = np.zeros(self.N)
+        self._check(self.lib.hf_apply_preconditioner(self.h, _ptr(x, C.c_double), _ptr(z, C.c_double)))
+        return z
+
+    def hf_set_profiling(self, on=True):
+        self._check(self.lib.hf_set_profiling(self.h, int(bool(on))))
+
+    def hf_get_kernel_times(self):
+        ms = np.zeros(8)
+        n = np.zeros(8, np.int64)
+        self._check(self.lib.hf_get_kernel_times(self.h, _ptr(ms, C.c_double), _ptr(n, C.c_int64)))
+        return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
+
+    def hf_get_stats(self):
+        st = np.zeros(8, np.int64)
+        self._check(self.lib.hf_get_stats(self.h, _ptr(st, C.c_int64)))
+        keys = ["elements", "interior_slots", "subdomain_slots", "levels_max", "subdomains", "nl_faces",
+                "n_p", "faces"]
+        return dict(zip(keys, (int(x) for x in st)))
+
+    def hf_solve_linear(self, rhs):
+        rhs = np.ascontiguousarray(rhs, dtype=np.float64)
+        d = np.zeros(self.N)
+        r = hf_newton_report()
+        self._check(self.lib.hf_solve_linear(self.h, _ptr(rhs, C.c_double), _ptr(d, C.c_double), C.byref(r)))
+        return d, r.as_dict()

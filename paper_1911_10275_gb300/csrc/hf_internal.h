@@ -1,0 +1,158 @@
+// hf_internal.h - the handle behind the C ABI and the kernel launchers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hf.h"
+#include "hf_core.cuh"
+
+namespace hfk {
+
+// kernel launchers (hf_assembly.cu)
+template <int DIM> void launch_geometry(const DevMesh& m, cudaStream_t st);
+template <int DIM>
+void launch_build_rows(const DevMesh& m, const Quad& q, const int* elist, int n, double* dg, double* off,
+                       cudaStream_t st);
+template <int DIM>
+void launch_neumann(const DevMesh& m, const Quad& q, const double* ftrac, const signed char* fneu,
+                    cudaStream_t st);
+template <int DIM> void launch_face_nl(const DevMesh& m, const Quad& q, const double* X, cudaStream_t st);
+template <int DIM>
+void launch_criterion(const DevMesh& m, const Quad& q, const double* X, double* tmax, int* n_new,
+                      cudaStream_t st);
+template <int DIM> void launch_openings(const DevMesh& m, const double* X, double* w, cudaStream_t st);
+template <int DIM>
+void launch_accept(const DevMesh& m, const Quad& q, const double* X, int* n_new, cudaStream_t st);
+void launch_fluid_scale(const DevMesh& m, int enabled, double L_ref, cudaStream_t st);
+
+// element-block matrix in structure-of-arrays form
+template <typename T> struct EBMat {
+  T* dg = nullptr;
+  T* off = nullptr;
+};
+
+// GMRES workspace of one precision
+template <typename T> struct Krylov {
+  T* V = nullptr;        // (m+1) basis vectors, stride ldv
+  T* w = nullptr;        // Arnoldi work vector
+  T* z = nullptr;        // preconditioned vector
+  T* u = nullptr;        // combination of the basis
+  T* x = nullptr;        // iterate
+  T* b = nullptr;        // right-hand side
+  T* lu = nullptr;       // ILU records
+  T* sinv = nullptr;     // pressure-row Schur diagonal (inverse)
+  long long ldv = 0;
+};
+
+// device scalars of the GMRES driver (one record, double precision)
+struct GmresState {
+  double H[31 * 30];     // Hessenberg, rotated in place (column-major, ld 31)
+  double g[31];
+  double cs[30], sn[30];
+  double y[30];
+  double inv_h;          // 1 / h(j+1, j)
+  double beta;           // residual norm of the cycle start
+  double tol_abs;        // absolute stopping threshold for |g(j+1)|
+  double nrm2;           // scratch reduction result
+  int done;
+  int jlast;
+  int iters;
+  int pad;
+};
+
+// event-timed kernel classes (profiling mode)
+enum ProfKind { PK_SPMV = 0, PK_PREC = 1, PK_ORTH = 2, PK_FACTOR = 3, PK_ASSEMBLY = 4, PK_SPMV64 = 5,
+                PK_UPDATE = 6, PK_COUNT = 8 };
+constexpr int PROF_EVENTS = 256;
+struct Prof {
+  bool on = false;
+  cudaEvent_t ev[2 * PROF_EVENTS] = {};
+  int kind[PROF_EVENTS] = {};
+  int n = 0;
+  double ms[PK_COUNT] = {};
+  long long launches[PK_COUNT] = {};
+};
+
+}  // namespace hfk
+
+struct hf_mesh {
+  int dim = 0, nen = 0, ned = 0, nfn = 0, nfr = 0;
+  long long ne = 0, nf = 0, nnodes = 0, nu = 0, np = 0, N = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::string err;
+  bool poisoned = false;
+  bool material_set = false, injection_set = false;
+
+  // host bookkeeping
+  std::vector<int> ext2int, int2ext;        // element permutation
+  std::vector<int> h_fe;                    // [s*nf + f] internal elements
+  std::vector<signed char> h_fl, h_crack, h_alpha, h_beta;
+  std::vector<int> h_nbr, h_slot_face;      // [j*ne + e]
+  std::vector<signed char> h_slot_side;
+  std::vector<long long> p_nodes;           // global node of each pressure unknown
+  std::vector<int> hp_fpdof;                // [a*nf + f] pressure unknown of face node a
+  int nl_cap = 0;                           // capacity of the nonlinear facet list
+  int levels_max = 0;                       // deepest level schedule of a subdomain
+  std::vector<int> sd_of;                   // subdomain of each internal element
+  std::vector<int> sd_always;               // subdomains with a cohesive slot
+  std::vector<int> sd_dirty;                // subdomains to refactor once
+
+  // device buffers
+  hfk::DevMesh d{};
+  hfk::Quad q{};
+  std::vector<void*> allocs;
+  hfk::EBMat<double> J64;
+  hfk::EBMat<float> J32;
+  bool j32_valid = false;
+  double* X = nullptr;         // state [U; P]
+  double* R = nullptr;         // residual
+  double* D = nullptr;         // Newton increment
+  double* tmp64 = nullptr;     // scratch
+  double* r64 = nullptr;       // IR residual
+  double* fneu_trac = nullptr; // [k*nf + f]
+  signed char* fneu = nullptr;
+  int* d_elist = nullptr;      // element list scratch
+  int* d_sdlist = nullptr;     // subdomain list scratch
+  int* d_count = nullptr;      // counters [0]: criterion, [1]: accept, [2..]: reduction counters
+  double* d_partial = nullptr; // block partials of reductions
+  double* d_red = nullptr;     // reduction results
+  double* d_wtmp = nullptr;    // facet opening scratch / criterion output
+  hfk::GmresState* d_gs = nullptr;
+  hfk::Krylov<double> K64;
+  hfk::Krylov<float> K32;
+  int red_blocks = 0;
+
+  // parameters
+  double E = 0, nu_p = 0, sigma_c = 0, delta_c = 0, b_stab = 10.0;
+  double mu_f = 0, Q0 = 0, delta_f = 0, dt = 1.0, p_v = 0, L_ref = 1.0;
+  int cutoff = 0;
+  double t = 0.0;
+  hf_solver_opts opts{};
+  int G = 0;                   // subdomain size in use
+
+  // CUDA graphs of one GMRES cycle per precision
+  cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
+  hfk::Prof prof;
+  long long n_interior_slots = 0, n_subdomain_slots = 0;
+};
+
+namespace hfk {
+// solver side (hf_solve.cu)
+hf_status solver_alloc(hf_mesh* h);
+void convert_j32(hf_mesh* h);
+void factor_subdomains(hf_mesh* h, const std::vector<int>& sds);
+hf_status residual(hf_mesh* h, const double* X, double* R);
+hf_status apply_jacobian(hf_mesh* h, const double* x, double* y);
+hf_status linear_solve(hf_mesh* h, const double* b, double* x, hf_newton_report* rep);
+hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]);
+double device_norm2(hf_mesh* h, const double* v, long long n);
+hf_status set_error(hf_mesh* h, hf_status s, const std::string& msg);
+hf_status check_cuda(hf_mesh* h, cudaError_t e, const char* where);
+// profiling: event pair around a kernel class; flush accumulates elapsed times
+void prof_begin(hf_mesh* h, int kind);
+void prof_end(hf_mesh* h);
+void prof_flush(hf_mesh* h);
+}  // namespace hfk

@@ -1,0 +1,1181 @@
+// hf_solve.cu - Krylov solve of the linearised system [A B; C D] d = -R
+// (Eq. fully-coupled-fully-discrete) on one GPU.
+//
+//  * SpMV: thread per element over the structure-of-arrays element-block CSR
+//    (coalesced matrix stream, element index fastest), plus the face-node
+//    terms of cohesive (alpha) and fluid (beta) facets, plus the pressure rows
+//    gathered per pressure unknown.  No atomics: every row has one writer.
+//  * Preconditioner: block-Jacobi over subdomains of G consecutive elements
+//    (Morton order); inside each subdomain a block ILU(0) of A with element
+//    blocks, applied by one CTA per subdomain with a level schedule (levels
+//    separated by __syncthreads, elements of a level spread over warps, lane =
+//    row).  Pressure rows: block lower-triangular step z_p = S^-1 (r_p - C z_u)
+//    with S the diagonal of D - C diag(A)^-1 B taken facet by facet.
+//  * GMRES(m), right preconditioned, classical Gram-Schmidt, Givens rotations
+//    on device; every reduction is two-level (block partials, last block
+//    reduces in fixed order) so results are deterministic.  A cycle of m
+//    iterations runs without host synchronisation; kernels after convergence
+//    see the done flag and return at once.
+//  * Mixed precision: FP32 matrix, factor and Krylov vectors inside FP64
+//    iterative refinement (residual and update in FP64).
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+
+#include "hf_internal.h"
+
+namespace hfk {
+
+constexpr int RB = 256;  // threads of reduction kernels
+
+template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
+
+// ------------------------------------------------------------------ SpMV
+// MODE 0: y = J x.  MODE 1 (T = double): y = R(x), the residual.
+template <typename T, int DIM, int MODE>
+__device__ void add_nl_terms(const DevMesh& m, int e, unsigned nlm, const T* __restrict__ x, T* y) {
+  using S = Shape<DIM>;
+  using L = NL<DIM>;
+  constexpr int F = S::nfn, NED = S::ned;
+  unsigned dmask = m.dirmask[e];
+  for (int j = 0; j < DIM + 1; ++j) {
+    bool al = (nlm >> j) & 1u, be = (nlm >> (4 + j)) & 1u;
+    if (!al && !be) continue;
+    int f = m.slot_face[j * m.ne + e];
+    int s = m.slot_side[j * m.ne + e];
+    const double* rec = m.nl + (long long)f * S::nld;
+    double n[DIM];
+    for (int k = 0; k < DIM; ++k) n[k] = m.fnormal[k * m.nf + f];
+    double val[F];
+    if (MODE == 0) {
+      int em = m.fe[f], ep = m.fe[m.nf + f];
+      double jn[F], xp[F];
+      for (int b = 0; b < F; ++b) {
+        int lm = m.loc_m[b * m.nf + f], lp = m.loc_p[b * m.nf + f];
+        double sacc = 0.0;
+        for (int k = 0; k < DIM; ++k)
+          sacc += n[k] * ((double)x[(long long)ep * NED + lp * DIM + k] - (double)x[(long long)em * NED + lm * DIM + k]);
+        jn[b] = sacc;
+        int pd = m.fpdof[b * m.nf + f];
+        xp[b] = (be && pd >= 0) ? (double)x[m.nu + pd] : 0.0;
+      }
+      for (int a = 0; a < F; ++a) {
+        double v = 0.0;
+        for (int b = 0; b < F; ++b) {
+          if (al) v += rec[L::Tm + a * F + b] * jn[b];
+          if (be) v -= rec[L::Mm + a * F + b] * xp[b];
+        }
+        val[a] = v;
+      }
+    } else {
+      for (int a = 0; a < F; ++a) val[a] = (al ? rec[L::rc + a] : 0.0) - (be ? rec[L::rp + a] : 0.0);
+    }
+    double sg = s == 0 ? -1.0 : 1.0;
+    for (int a = 0; a < F; ++a) {
+      int loc = s == 0 ? m.loc_m[a * m.nf + f] : m.loc_p[a * m.nf + f];
+      for (int k = 0; k < DIM; ++k) {
+        int row = loc * DIM + k;
+        if (!((dmask >> row) & 1u)) y[(long long)e * NED + row] += (T)(sg * n[k] * val[a]);
+      }
+    }
+  }
+}
+
+template <typename T, int DIM, int MODE>
+__device__ void pressure_row(const DevMesh& m, int g, const T* __restrict__ x, T* __restrict__ y) {
+  using S = Shape<DIM>;
+  using L = NL<DIM>;
+  constexpr int F = S::nfn, NED = S::ned;
+  double c = m.scal[0];
+  if (!m.p_active[g]) {
+    y[m.nu + g] = (MODE == 0) ? x[m.nu + g] : (T)((double)x[m.nu + g] - m.p_v);
+    return;
+  }
+  double acc = 0.0;
+  for (int t = m.pinc_ptr[g]; t < m.pinc_ptr[g + 1]; ++t) {
+    int f = m.pinc_face[t];
+    if (!m.beta[f]) continue;
+    int ga = m.pinc_a[t];
+    const double* rec = m.nl + (long long)f * S::nld;
+    if (MODE == 0) {
+      int em = m.fe[f], ep = m.fe[m.nf + f];
+      for (int b = 0; b < F; ++b) {
+        int lm = m.loc_m[b * m.nf + f], lp = m.loc_p[b * m.nf + f];
+        double jn = 0.0;
+        for (int k = 0; k < DIM; ++k)
+          jn += m.fnormal[k * m.nf + f] *
+                ((double)x[(long long)ep * NED + lp * DIM + k] - (double)x[(long long)em * NED + lm * DIM + k]);
+        acc += rec[L::Cs + ga * F + b] * jn;
+        int pd = m.fpdof[b * m.nf + f];
+        acc += rec[L::Dm + ga * F + b] * (double)x[m.nu + pd];
+      }
+    } else {
+      acc += rec[L::rf + ga];
+    }
+  }
+  if (MODE == 1) acc -= m.Q0 * m.inj_w[g];
+  y[m.nu + g] = (T)(c * acc);
+}
+
+template <typename T, int DIM, int MODE>
+__global__ void __launch_bounds__(128) k_spmv(DevMesh m, const T* __restrict__ dg, const T* __restrict__ off,
+                                              const T* __restrict__ x, T* __restrict__ y, int eblocks,
+                                              const int* skip) {
+  using S = Shape<DIM>;
+  constexpr int NED = S::ned, NFR = S::nfr;
+  if (skip && *skip) return;
+  if ((int)blockIdx.x >= eblocks) {
+    int g = (blockIdx.x - eblocks) * blockDim.x + threadIdx.x;
+    if (g < m.np) pressure_row<T, DIM, MODE>(m, g, x, y);
+    return;
+  }
+  int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= m.ne) return;
+  const long long ne = m.ne;
+  T acc[NED];
+#pragma unroll
+  for (int r = 0; r < NED; ++r) acc[r] = (T)0;
+  const T* xe = x + (long long)e * NED;
+  const T* dge = dg + e;
+#pragma unroll 2
+  for (int c = 0; c < NED; ++c) {
+    T xc = xe[c];
+    const T* col = dge + (long long)c * NED * ne;
+#pragma unroll
+    for (int r = 0; r < NED; ++r) acc[r] += ld(col + r * ne) * xc;
+  }
+#pragma unroll
+  for (int j = 0; j < DIM + 1; ++j) {
+    int nb = m.nbr[j * ne + e];
+    if (nb >= 0) {
+      const T* xn = x + (long long)nb * NED;
+      const T* ob = off + (long long)j * NED * NFR * ne + e;
+#pragma unroll 2
+      for (int c = 0; c < NED; ++c) {
+        T xc = xn[c];
+        const T* col = ob + (long long)c * NFR * ne;
+#pragma unroll
+        for (int rr = 0; rr < NFR; ++rr)
+          acc[face_node<DIM>(j, rr / DIM) * DIM + rr % DIM] += ld(col + rr * ne) * xc;
+      }
+    }
+  }
+  T* ye = y + (long long)e * NED;
+  if (MODE == 1) {
+    unsigned dm = m.dirmask[e];
+#pragma unroll
+    for (int r = 0; r < NED; ++r)
+      acc[r] -= (T)(((dm >> r) & 1u) ? m.ubar[(long long)e * NED + r] : m.fext[(long long)e * NED + r]);
+  }
+#pragma unroll
+  for (int r = 0; r < NED; ++r) ye[r] = acc[r];
+  unsigned nlm = m.nlmask[e];
+  if (nlm) add_nl_terms<T, DIM, MODE>(m, e, nlm, x, y);
+}
+
+// ------------------------------------------------------------------ ILU(0)
+// Row-major scratch per warp: Am (ned x ned) and Lm (nfr x ned).
+template <typename T, int DIM>
+__device__ void cohesive_patch_rows(const DevMesh& m, int i, int j, int nbside, T* M, int ldm, bool diag,
+                                    int lane) {
+  // adds alpha * sigma_s sigma_t n_k n_l Tm_ab for the facet of slot j of element i;
+  // diag: target is A_ii (rows = element rows); else A_i,nb compact (rows = face rows of slot j)
+  using S = Shape<DIM>;
+  using L = NL<DIM>;
+  constexpr int F = S::nfn;
+  int f = m.slot_face[j * m.ne + i];
+  int s = m.slot_side[j * m.ne + i];
+  const double* rec = m.nl + (long long)f * S::nld;
+  unsigned dmask = m.dirmask[i];
+  double sgn = diag ? 1.0 : -1.0;
+  for (int t = lane; t < F * F * DIM * DIM; t += 32) {
+    int ab = t / (DIM * DIM), kl = t % (DIM * DIM);
+    int a = ab / F, b = ab % F, k = kl / DIM, l = kl % DIM;
+    int la = s == 0 ? m.loc_m[a * m.nf + f] : m.loc_p[a * m.nf + f];
+    int row_el = la * DIM + k;
+    if ((dmask >> row_el) & 1u) continue;
+    int ts = diag ? s : 1 - s;
+    int lb = ts == 0 ? m.loc_m[b * m.nf + f] : m.loc_p[b * m.nf + f];
+    int col = lb * DIM + l;
+    int row = row_el;
+    if (!diag) {
+      int fa = 0;
+      for (int q = 0; q < F; ++q)
+        if (face_node<DIM>(j, q) == la) fa = q;
+      row = fa * DIM + k;
+    }
+    double v = sgn * m.fnormal[k * m.nf + f] * m.fnormal[l * m.nf + f] * rec[L::Tm + a * F + b];
+    M[row * ldm + col] += (T)v;
+  }
+  (void)nbside;
+}
+
+template <typename T, int DIM>
+__device__ void warp_invert(T* A, int lane) {
+  constexpr int N = Shape<DIM>::ned;
+  int piv[N];
+#pragma unroll
+  for (int k = 0; k < N; ++k) {
+    // pivot: largest |A[i][k]| for i >= k
+    T v = (lane >= k && lane < N) ? (T)fabs((double)A[lane * N + k]) : (T)-1;
+    int idx = lane;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      T ov = __shfl_xor_sync(0xffffffffu, v, o);
+      int oi = __shfl_xor_sync(0xffffffffu, idx, o);
+      if (ov > v || (ov == v && oi < idx)) {
+        v = ov;
+        idx = oi;
+      }
+    }
+    int p = idx;
+    piv[k] = p;
+    if (p != k && lane < N) {
+      T t = A[k * N + lane];
+      A[k * N + lane] = A[p * N + lane];
+      A[p * N + lane] = t;
+    }
+    __syncwarp();
+    T pinv = (T)1 / A[k * N + k];
+    __syncwarp();
+    if (lane < N && lane != k) A[k * N + lane] *= pinv;
+    __syncwarp();
+    T fk = (lane < N) ? A[lane * N + k] : (T)0;
+    __syncwarp();
+    if (lane < N && lane != k) {
+      for (int c = 0; c < N; ++c)
+        if (c != k) A[lane * N + c] -= fk * A[k * N + c];
+      A[lane * N + k] = -fk * pinv;
+    }
+    __syncwarp();
+    if (lane == 0) A[k * N + k] = pinv;
+    __syncwarp();
+  }
+#pragma unroll
+  for (int k = N - 1; k >= 0; --k) {
+    int p = piv[k];
+    if (p != k && lane < N) {
+      T t = A[lane * N + k];
+      A[lane * N + k] = A[lane * N + p];
+      A[lane * N + p] = t;
+    }
+    __syncwarp();
+  }
+}
+
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __restrict__ dg,
+                                                    const double* __restrict__ off, T* lu, const int* sdlist) {
+  using S = Shape<DIM>;
+  constexpr int NED = S::ned, NFR = S::nfr, LUS = S::lus;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  T* Am = reinterpret_cast<T*>(smraw) + warp * (NED * NED + NFR * NED);
+  T* Lm = Am + NED * NED;
+  int s = sdlist[blockIdx.x];
+  int lb = m.sd_lvl_base[s], nl = m.sd_nlvl[s];
+  const long long ne = m.ne;
+  for (int lv = 0; lv < nl; ++lv) {
+    int lo = m.sd_lvl[lb + lv], hi = m.sd_lvl[lb + lv + 1];
+    for (int idx = lo + warp; idx < hi; idx += nw) {
+      int i = m.sd_elems[idx];
+      T* rec = lu + (long long)i * LUS;
+      unsigned nlm = m.nlmask[i];
+      for (int t = lane; t < NED * NED; t += 32) {
+        int r = t / NED, c = t % NED;
+        Am[r * NED + c] = (T)dg[((long long)c * NED + r) * ne + i];
+      }
+      __syncwarp();
+      for (int j = 0; j < DIM + 1; ++j) {
+        if ((nlm >> j) & 1u) cohesive_patch_rows<T, DIM>(m, i, j, 0, Am, NED, true, lane);
+        __syncwarp();
+      }
+      unsigned low = m.lowmask[i], up = m.upmask[i];
+      for (int j = 0; j < DIM + 1; ++j) {
+        if (!((low >> j) & 1u)) continue;
+        int k = m.nbr[j * ne + i];
+        // A_ik (compact) into Lm
+        for (int t = lane; t < NFR * NED; t += 32) {
+          int rr = t / NED, c = t % NED;
+          Lm[rr * NED + c] = (T)off[(((long long)j * NED + c) * NFR + rr) * ne + i];
+        }
+        __syncwarp();
+        if ((nlm >> j) & 1u) cohesive_patch_rows<T, DIM>(m, i, j, 1, Lm, NED, false, lane);
+        __syncwarp();
+        // L_ik = A_ik Dinv_k
+        const T* dk = lu + (long long)k * LUS;
+        T lrow[NED];
+        if (lane < NFR) {
+#pragma unroll
+          for (int c = 0; c < NED; ++c) lrow[c] = (T)0;
+          for (int mm = 0; mm < NED; ++mm) {
+            T a = Lm[lane * NED + mm];
+#pragma unroll
+            for (int c = 0; c < NED; ++c) lrow[c] += a * dk[c * NED + mm];
+          }
+        }
+        __syncwarp();
+        if (lane < NFR) {
+#pragma unroll
+          for (int c = 0; c < NED; ++c) {
+            Lm[lane * NED + c] = lrow[c];
+            rec[NED * NED + j * NED * NFR + c * NFR + lane] = lrow[c];
+          }
+        }
+        __syncwarp();
+        // A_ii -= L_ik U_ki, U_ki stored in k's slot that points back to i
+        int jk = 0;
+        for (int t = 0; t < DIM + 1; ++t)
+          if (m.nbr[t * ne + k] == i) jk = t;
+        const T* uk = lu + (long long)k * LUS + NED * NED + jk * NED * NFR;
+        for (int t = lane; t < NFR * NED; t += 32) {
+          int rr = t / NED, c = t % NED;
+          T sacc = (T)0;
+          for (int r2 = 0; r2 < NFR; ++r2) {
+            int rowk = face_node<DIM>(jk, r2 / DIM) * DIM + r2 % DIM;
+            sacc += Lm[rr * NED + rowk] * uk[c * NFR + r2];
+          }
+          int rowi = face_node<DIM>(j, rr / DIM) * DIM + rr % DIM;
+          Am[rowi * NED + c] -= sacc;
+        }
+        __syncwarp();
+      }
+      for (int j = 0; j < DIM + 1; ++j) {
+        if (!((up >> j) & 1u)) continue;
+        for (int t = lane; t < NFR * NED; t += 32) {
+          int rr = t / NED, c = t % NED;
+          Lm[rr * NED + c] = (T)off[(((long long)j * NED + c) * NFR + rr) * ne + i];
+        }
+        __syncwarp();
+        if ((nlm >> j) & 1u) cohesive_patch_rows<T, DIM>(m, i, j, 1, Lm, NED, false, lane);
+        __syncwarp();
+        for (int t = lane; t < NFR * NED; t += 32) {
+          int rr = t / NED, c = t % NED;
+          rec[NED * NED + j * NED * NFR + c * NFR + rr] = Lm[rr * NED + c];
+        }
+        __syncwarp();
+      }
+      warp_invert<T, DIM>(Am, lane);
+      for (int t = lane; t < NED * NED; t += 32) {
+        int c = t / NED, r = t % NED;
+        rec[c * NED + r] = Am[r * NED + c];
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+}
+
+// Schur diagonal of the pressure rows: S = c sum_f [Dm_gg + sum_ab Cs_gb M_ag n.Dinv_(b,a).n]
+template <typename T, int DIM>
+__global__ void k_schur(DevMesh m, const T* __restrict__ lu, T* sinv) {
+  using S = Shape<DIM>;
+  using L = NL<DIM>;
+  constexpr int F = S::nfn, NED = S::ned, LUS = S::lus;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m.np) return;
+  if (!m.p_active[g]) {
+    sinv[g] = (T)1;
+    return;
+  }
+  double c = m.scal[0], sacc = 0.0;
+  for (int t = m.pinc_ptr[g]; t < m.pinc_ptr[g + 1]; ++t) {
+    int f = m.pinc_face[t];
+    if (!m.beta[f]) continue;
+    int ga = m.pinc_a[t];
+    const double* rec = m.nl + (long long)f * S::nld;
+    double n[DIM];
+    for (int k = 0; k < DIM; ++k) n[k] = m.fnormal[k * m.nf + f];
+    double v = rec[L::Dm + ga * F + ga];
+    for (int s = 0; s < 2; ++s) {
+      int e = m.fe[s * m.nf + f];
+      const T* di = lu + (long long)e * LUS;
+      for (int b = 0; b < F; ++b) {
+        int lb = s == 0 ? m.loc_m[b * m.nf + f] : m.loc_p[b * m.nf + f];
+        double cs = rec[L::Cs + ga * F + b];
+        for (int a = 0; a < F; ++a) {
+          int la = s == 0 ? m.loc_m[a * m.nf + f] : m.loc_p[a * m.nf + f];
+          double nd = 0.0;
+          for (int l = 0; l < DIM; ++l)
+            for (int k = 0; k < DIM; ++k)
+              nd += n[l] * (double)di[(la * DIM + k) * NED + (lb * DIM + l)] * n[k];
+          v += cs * rec[L::Mm + a * F + ga] * nd;
+        }
+      }
+    }
+    sacc += v;
+  }
+  double Sg = c * sacc;
+  if (!(fabs(Sg) > 1e-300)) Sg = 1.0;
+  sinv[g] = (T)(1.0 / Sg);
+}
+
+// z = M^-1 (scale * rin); optionally writes v = scale * rin.  One CTA per subdomain.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(128) k_ilu_apply(DevMesh m, const T* __restrict__ lu, const T* __restrict__ rin,
+                                                   const double* scale, T* vout, T* z, const int* skip) {
+  using S = Shape<DIM>;
+  constexpr int NED = S::ned, NFR = S::nfr, LUS = S::lus;
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) unsigned char smraw[];
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int s = blockIdx.x;
+  int base = s * m.G;
+  int cnt = min(m.G, m.ne - base);
+  T* ys = reinterpret_cast<T*>(smraw);
+  T* tmp = ys + m.G * NED + warp * 32;
+  T sc = scale ? (T)(*scale) : (T)1;
+  for (int t = threadIdx.x; t < cnt * NED; t += blockDim.x) {
+    T v = rin[(long long)base * NED + t] * sc;
+    ys[t] = v;
+    if (vout) vout[(long long)base * NED + t] = v;
+  }
+  __syncthreads();
+  int lb = m.sd_lvl_base[s], nl = m.sd_nlvl[s];
+  const long long ne = m.ne;
+  // forward: y_i = r_i - sum_{k lower} L_ik y_k
+  for (int lv = 0; lv < nl; ++lv) {
+    int lo = m.sd_lvl[lb + lv], hi = m.sd_lvl[lb + lv + 1];
+    for (int idx = lo + warp; idx < hi; idx += nw) {
+      int i = m.sd_elems[idx];
+      int li = i - base;
+      unsigned low = m.lowmask[i];
+      const T* rec = lu + (long long)i * LUS;
+      for (int j = 0; j < DIM + 1; ++j) {
+        if (!((low >> j) & 1u)) continue;
+        int lk = m.nbr[j * ne + i] - base;
+        const T* blk = rec + NED * NED + j * NED * NFR;
+        T dot = (T)0;
+        if (lane < NFR) {
+#pragma unroll 6
+          for (int c = 0; c < NED; ++c) dot += blk[c * NFR + lane] * ys[lk * NED + c];
+        }
+        __syncwarp();
+        if (lane < NFR) ys[li * NED + face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= dot;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+  }
+  // backward: z_i = Dinv_i (y_i - sum_{j upper} U_ij z_j)
+  for (int lv = nl - 1; lv >= 0; --lv) {
+    int lo = m.sd_lvl[lb + lv], hi = m.sd_lvl[lb + lv + 1];
+    for (int idx = lo + warp; idx < hi; idx += nw) {
+      int i = m.sd_elems[idx];
+      int li = i - base;
+      unsigned up = m.upmask[i];
+      const T* rec = lu + (long long)i * LUS;
+      if (lane < NED) tmp[lane] = ys[li * NED + lane];
+      __syncwarp();
+      for (int j = 0; j < DIM + 1; ++j) {
+        if (!((up >> j) & 1u)) continue;
+        int lk = m.nbr[j * ne + i] - base;
+        const T* blk = rec + NED * NED + j * NED * NFR;
+        T dot = (T)0;
+        if (lane < NFR) {
+#pragma unroll 6
+          for (int c = 0; c < NED; ++c) dot += blk[c * NFR + lane] * ys[lk * NED + c];
+        }
+        __syncwarp();
+        if (lane < NFR) tmp[face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= dot;
+        __syncwarp();
+      }
+      T zr = (T)0;
+      if (lane < NED) {
+#pragma unroll 6
+        for (int c = 0; c < NED; ++c) zr += rec[c * NED + lane] * tmp[c];
+      }
+      __syncwarp();
+      if (lane < NED) ys[li * NED + lane] = zr;
+      __syncwarp();
+    }
+    __syncthreads();
+  }
+  for (int t = threadIdx.x; t < cnt * NED; t += blockDim.x) z[(long long)base * NED + t] = ys[t];
+}
+
+// pressure part of the preconditioner (after the displacement part)
+template <typename T, int DIM>
+__global__ void k_prec_p(DevMesh m, const T* __restrict__ rin, const double* scale, T* vout, const T* __restrict__ sinv,
+                         T* z, const int* skip) {
+  using S = Shape<DIM>;
+  using L = NL<DIM>;
+  constexpr int F = S::nfn, NED = S::ned;
+  if (skip && *skip) return;
+  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m.np) return;
+  T sc = scale ? (T)(*scale) : (T)1;
+  T r = rin[m.nu + g] * sc;
+  if (vout) vout[m.nu + g] = r;
+  if (!m.p_active[g]) {
+    z[m.nu + g] = r;
+    return;
+  }
+  double acc = 0.0;
+  for (int t = m.pinc_ptr[g]; t < m.pinc_ptr[g + 1]; ++t) {
+    int f = m.pinc_face[t];
+    if (!m.beta[f]) continue;
+    int ga = m.pinc_a[t];
+    const double* rec = m.nl + (long long)f * S::nld;
+    int em = m.fe[f], ep = m.fe[m.nf + f];
+    for (int b = 0; b < F; ++b) {
+      int lm = m.loc_m[b * m.nf + f], lp = m.loc_p[b * m.nf + f];
+      double jn = 0.0;
+      for (int k = 0; k < DIM; ++k)
+        jn += m.fnormal[k * m.nf + f] *
+              ((double)z[(long long)ep * NED + lp * DIM + k] - (double)z[(long long)em * NED + lm * DIM + k]);
+      acc += rec[L::Cs + ga * F + b] * jn;
+    }
+  }
+  z[m.nu + g] = (T)(((double)r - m.scal[0] * acc) * (double)sinv[g]);
+}
+
+// ------------------------------------------------------------------ reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// block sum of v into partial[blockIdx.x]; returns true in the last block
+// (after all partials are visible), where thread 0 may combine them
+__device__ bool block_partial_last(double v, double* partial, int* counter) {
+  __shared__ double sm[32];
+  __shared__ bool last;
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  v = warp_sum(v);
+  if (lane == 0) sm[warp] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s += sm[w];
+    partial[blockIdx.x] = s;
+    __threadfence();
+    int t = atomicAdd(counter, 1);
+    last = (t == (int)gridDim.x - 1);
+  }
+  __syncthreads();
+  return last;
+}
+
+__device__ double sum_partials(const double* partial, int n) {
+  const volatile double* p = partial;
+  double s = 0.0;
+  for (int b = 0; b < n; ++b) s += p[b];
+  return s;
+}
+
+// multi-dot: H[:, j] = V[:, 0..j]^T w
+template <typename T>
+__global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long ldv, int j, const T* __restrict__ w,
+                                             long long n, double* partial, int* counter, GmresState* gs) {
+  if (gs->done) return;
+  __shared__ double sm[RB / 32][32];
+  __shared__ bool last;
+  int ncols = j + 1;
+  T acc[32];
+#pragma unroll
+  for (int c = 0; c < 32; ++c) acc[c] = (T)0;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T wv = w[i];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < ncols) acc[c] += V[c * ldv + i] * wv;
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int c = 0; c < 32; ++c) {
+    if (c < ncols) {
+      double v = warp_sum((double)acc[c]);
+      if (lane == 0) sm[warp][c] = v;
+    }
+  }
+  __syncthreads();
+  if (threadIdx.x < ncols) {
+    double s = 0.0;
+    for (int wq = 0; wq < RB / 32; ++wq) s += sm[wq][threadIdx.x];
+    partial[blockIdx.x * 32 + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (last) {
+    if (threadIdx.x < ncols) {
+      const volatile double* p = partial;
+      double s = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += p[b * 32 + threadIdx.x];
+      gs->H[j * 31 + threadIdx.x] = s;
+    }
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+// w -= V h; ||w||; Givens update of column j; convergence test
+template <typename T>
+__global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
+                                             double* partial, int* counter, GmresState* gs, int mrest) {
+  if (gs->done) return;
+  __shared__ T h[32];
+  int ncols = j + 1;
+  if (threadIdx.x < 32) h[threadIdx.x] = threadIdx.x < ncols ? (T)gs->H[j * 31 + threadIdx.x] : (T)0;
+  __syncthreads();
+  double acc = 0.0;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T ww = w[i];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < ncols) ww -= h[c] * V[c * ldv + i];
+    w[i] = ww;
+    acc += (double)ww * (double)ww;
+  }
+  if (block_partial_last(acc, partial, counter) && threadIdx.x == 0) {
+    double nrm = sqrt(sum_partials(partial, gridDim.x));
+    double* hc = gs->H + j * 31;
+    for (int i = 0; i < j; ++i) {
+      double a = hc[i], b = hc[i + 1];
+      hc[i] = gs->cs[i] * a + gs->sn[i] * b;
+      hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b;
+    }
+    double a = hc[j];
+    double den = hypot(a, nrm);
+    double cs = den > 0.0 ? a / den : 1.0, sn = den > 0.0 ? nrm / den : 0.0;
+    hc[j] = den;
+    hc[j + 1] = 0.0;
+    gs->cs[j] = cs;
+    gs->sn[j] = sn;
+    gs->g[j + 1] = -sn * gs->g[j];
+    gs->g[j] = cs * gs->g[j];
+    gs->inv_h = nrm > 0.0 ? 1.0 / nrm : 0.0;
+    gs->iters += 1;
+    gs->jlast = j + 1;
+    if (fabs(gs->g[j + 1]) <= gs->tol_abs || j + 1 >= mrest || !(nrm > 0.0) || !isfinite(nrm)) gs->done = 1;
+    *counter = 0;
+  }
+}
+
+template <typename T>
+__global__ void k_scale_into(const T* __restrict__ w, T* v, long long n, const double* s, const int* skip) {
+  if (skip && *skip) return;
+  T sc = (T)(*s);
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) v[i] = w[i] * sc;
+}
+
+__global__ void k_backsolve(GmresState* gs) {
+  if (threadIdx.x != 0) return;
+  int jl = gs->jlast;
+  for (int i = jl - 1; i >= 0; --i) {
+    double s = gs->g[i];
+    for (int k = i + 1; k < jl; ++k) s -= gs->H[k * 31 + i] * gs->y[k];
+    double d = gs->H[i * 31 + i];
+    gs->y[i] = d != 0.0 ? s / d : 0.0;
+  }
+}
+
+template <typename T>
+__global__ void k_combine(const T* __restrict__ V, long long ldv, long long n, const GmresState* gs, T* u) {
+  __shared__ T y[32];
+  int jl = gs->jlast;
+  if (threadIdx.x < 32) y[threadIdx.x] = threadIdx.x < jl ? (T)gs->y[threadIdx.x] : (T)0;
+  __syncthreads();
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T s = (T)0;
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < jl) s += y[c] * V[c * ldv + i];
+    u[i] = s;
+  }
+}
+
+template <typename T>
+__global__ void k_axpy(T* x, const T* __restrict__ z, long long n) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) x[i] += z[i];
+}
+
+// r = b - Ax and the start of a GMRES cycle: beta = ||r||, g = beta e1
+template <typename T>
+__global__ void __launch_bounds__(RB) k_residual_start(const T* __restrict__ b, const T* __restrict__ Ax, T* r, long long n,
+                                                       double* partial, int* counter, GmresState* gs, double tol_abs) {
+  double acc = 0.0;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+    T v = b[i] - (Ax ? Ax[i] : (T)0);
+    r[i] = v;
+    acc += (double)v * (double)v;
+  }
+  if (block_partial_last(acc, partial, counter) && threadIdx.x == 0) {
+    double beta = sqrt(sum_partials(partial, gridDim.x));
+    gs->beta = beta;
+    for (int i = 0; i < 31; ++i) gs->g[i] = 0.0;
+    gs->g[0] = beta;
+    gs->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
+    gs->tol_abs = tol_abs;
+    gs->done = (beta <= tol_abs || !(beta > 0.0)) ? 1 : 0;
+    gs->jlast = 0;
+    *counter = 0;
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(RB) k_norm2(const T* __restrict__ v, long long n, double* partial, int* counter,
+                                              double* out) {
+  double acc = 0.0;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+    acc += (double)v[i] * (double)v[i];
+  if (block_partial_last(acc, partial, counter) && threadIdx.x == 0) {
+    *out = sum_partials(partial, gridDim.x);
+    *counter = 0;
+  }
+}
+
+// FP64 -> FP32 copy scaled by 1/||r|| (red[0] = ||r||^2)
+__global__ void k_demote_scaled(const double* __restrict__ r, float* b, long long n, const double* red) {
+  double s = 1.0 / sqrt(*red);
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (float)(r[i] * s);
+}
+__global__ void k_promote_axpy(double* x, const float* __restrict__ d, long long n, const double* red) {
+  double s = sqrt(*red);
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) x[i] += s * (double)d[i];
+}
+template <typename T>
+__global__ void k_fill(T* x, long long n, T v) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) x[i] = v;
+}
+__global__ void k_d2f(const double* __restrict__ a, float* b, long long n) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (float)a[i];
+}
+__global__ void k_f2d(const float* __restrict__ a, double* b, long long n) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = (double)a[i];
+}
+__global__ void k_neg(const double* __restrict__ a, double* b, long long n) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = -a[i];
+}
+
+// Newton update: X += D, optional cut-off p >= p_v on active pressures, and
+// the four squared norms ||dU||, ||U||, ||dP||, ||P|| (out[0..3])
+__global__ void __launch_bounds__(RB) k_newton_update(DevMesh m, double* X, const double* __restrict__ Dx,
+                                                      double* partial, int* counter, double* out) {
+  __shared__ double sm[4][RB / 32];
+  __shared__ bool last;
+  double a[4] = {0, 0, 0, 0};
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m.N; i += stride) {
+    double d = Dx[i];
+    double x = X[i] + d;
+    bool isp = i >= m.nu;
+    if (isp && m.cutoff && m.p_active[i - m.nu] && x < m.p_v) x = m.p_v;
+    X[i] = x;
+    a[isp ? 2 : 0] += d * d;
+    a[isp ? 3 : 1] += x * x;
+  }
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int t = 0; t < 4; ++t) {
+    double v = warp_sum(a[t]);
+    if (lane == 0) sm[t][warp] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < 4) {
+    double s = 0.0;
+    for (int w = 0; w < RB / 32; ++w) s += sm[threadIdx.x][w];
+    partial[blockIdx.x * 4 + threadIdx.x] = s;
+  }
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
+  __syncthreads();
+  if (last && threadIdx.x < 4) {
+    const volatile double* p = partial;
+    double s = 0.0;
+    for (int b = 0; b < (int)gridDim.x; ++b) s += p[b * 4 + threadIdx.x];
+    out[threadIdx.x] = s;
+    __syncwarp(0xfu);
+    if (threadIdx.x == 0) *counter = 0;
+  }
+}
+
+// ------------------------------------------------------------------ host side
+hf_status set_error(hf_mesh* h, hf_status s, const std::string& msg) {
+  h->err = msg;
+  return s;
+}
+hf_status check_cuda(hf_mesh* h, cudaError_t e, const char* where) {
+  if (e == cudaSuccess) return HF_OK;
+  h->poisoned = true;
+  h->err = std::string(where) + ": " + cudaGetErrorString(e);
+  return HF_ERR_CUDA;
+}
+
+// ---------------------------------------------------------------- profiling
+// Event pairs are recorded only when profiling is on and the GMRES cycle is
+// not captured in a graph; elapsed times are read at the next synchronisation.
+void prof_begin(hf_mesh* h, int kind) {
+  Prof& p = h->prof;
+  if (!p.on) return;
+  if (p.n >= PROF_EVENTS) prof_flush(h);
+  if (!p.ev[2 * p.n]) {
+    cudaEventCreate(&p.ev[2 * p.n]);
+    cudaEventCreate(&p.ev[2 * p.n + 1]);
+  }
+  p.kind[p.n] = kind;
+  cudaEventRecord(p.ev[2 * p.n], h->stream);
+}
+void prof_end(hf_mesh* h) {
+  Prof& p = h->prof;
+  if (!p.on) return;
+  cudaEventRecord(p.ev[2 * p.n + 1], h->stream);
+  p.n += 1;
+}
+void prof_flush(hf_mesh* h) {
+  Prof& p = h->prof;
+  if (!p.on || p.n == 0) return;
+  cudaEventSynchronize(p.ev[2 * p.n - 1]);
+  for (int i = 0; i < p.n; ++i) {
+    float ms = 0.0f;
+    cudaEventElapsedTime(&ms, p.ev[2 * i], p.ev[2 * i + 1]);
+    p.ms[p.kind[i]] += ms;
+    p.launches[p.kind[i]] += 1;
+  }
+  p.n = 0;
+}
+
+static int grid_for(long long n, int threads, int cap) {
+  long long b = (n + threads - 1) / threads;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+template <typename T> static T* dalloc(hf_mesh* h, size_t n) {
+  void* p = nullptr;
+  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
+  h->allocs.push_back(p);
+  return reinterpret_cast<T*>(p);
+}
+
+hf_status solver_alloc(hf_mesh* h) {
+  long long N = h->N;
+  int m = 30;
+  long long ldv = (N + 63) / 64 * 64;
+  h->red_blocks = 152 * 4;
+  h->K64.ldv = ldv;
+  h->K32.ldv = ldv;
+  h->K64.V = dalloc<double>(h, (size_t)ldv * (m + 1));
+  h->K64.w = dalloc<double>(h, N);
+  h->K64.z = dalloc<double>(h, N);
+  h->K64.u = dalloc<double>(h, N);
+  h->K64.x = dalloc<double>(h, N);
+  h->K64.b = dalloc<double>(h, N);
+  h->K32.V = dalloc<float>(h, (size_t)ldv * (m + 1));
+  h->K32.w = dalloc<float>(h, N);
+  h->K32.z = dalloc<float>(h, N);
+  h->K32.u = dalloc<float>(h, N);
+  h->K32.x = dalloc<float>(h, N);
+  h->K32.b = dalloc<float>(h, N);
+  size_t lus = (size_t)h->ne * (h->dim == 2 ? Shape<2>::lus : Shape<3>::lus);
+  h->K64.lu = dalloc<double>(h, lus);
+  h->K32.lu = dalloc<float>(h, lus);
+  h->K64.sinv = dalloc<double>(h, h->np > 0 ? h->np : 1);
+  h->K32.sinv = dalloc<float>(h, h->np > 0 ? h->np : 1);
+  size_t nmat = (size_t)h->ne * (h->ned * h->ned + (h->dim + 1) * h->ned * h->nfr);
+  h->J32.dg = dalloc<float>(h, nmat);
+  h->J32.off = h->J32.dg + (size_t)h->ne * h->ned * h->ned;
+  h->d_partial = dalloc<double>(h, (size_t)h->red_blocks * 32);
+  h->d_gs = dalloc<GmresState>(h, 1);
+  if (!h->K64.V || !h->K64.w || !h->K64.z || !h->K64.u || !h->K64.x || !h->K64.b || !h->K32.V ||
+      !h->K32.w || !h->K32.z || !h->K32.u || !h->K32.x || !h->K32.b || !h->K64.lu || !h->K32.lu ||
+      !h->K64.sinv || !h->K32.sinv || !h->J32.dg || !h->d_partial || !h->d_gs)
+    return set_error(h, HF_ERR_OOM, "device allocation of the solver workspace failed");
+  cudaMemsetAsync(h->K64.lu, 0, lus * sizeof(double), h->stream);
+  cudaMemsetAsync(h->K32.lu, 0, lus * sizeof(float), h->stream);
+  cudaMemsetAsync(h->d_gs, 0, sizeof(GmresState), h->stream);
+  return HF_OK;
+}
+
+void convert_j32(hf_mesh* h) {
+  size_t nmat = (size_t)h->ne * (h->ned * h->ned + (h->dim + 1) * h->ned * h->nfr);
+  k_d2f<<<grid_for(nmat, 256, 152 * 16), 256, 0, h->stream>>>(h->J64.dg, h->J32.dg, nmat);
+  h->j32_valid = true;
+}
+
+template <int DIM> static size_t factor_smem(int elem_size) {
+  using S = Shape<DIM>;
+  return (size_t)4 * (S::ned * S::ned + S::nfr * S::ned) * elem_size;
+}
+
+template <typename T, int DIM> static void factor_impl(hf_mesh* h, const std::vector<int>& sds, T* lu, T* sinv) {
+  if (!sds.empty()) {
+    cudaMemcpyAsync(h->d_sdlist, sds.data(), sds.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
+    size_t sm = factor_smem<DIM>(sizeof(T));
+    cudaFuncSetAttribute(k_ilu_factor<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_ilu_factor<T, DIM><<<(int)sds.size(), 128, sm, h->stream>>>(h->d, h->J64.dg, h->J64.off, lu, h->d_sdlist);
+  }
+  if (h->np > 0) k_schur<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, lu, sinv);
+}
+
+void factor_subdomains(hf_mesh* h, const std::vector<int>& sds) {
+  bool mixed = h->opts.precision == HF_PREC_MIXED;
+  prof_begin(h, PK_FACTOR);
+  struct End {
+    hf_mesh* h;
+    ~End() { prof_end(h); }
+  } end_{h};
+  if (h->dim == 2) {
+    if (mixed) factor_impl<float, 2>(h, sds, h->K32.lu, h->K32.sinv);
+    else factor_impl<double, 2>(h, sds, h->K64.lu, h->K64.sinv);
+  } else {
+    if (mixed) factor_impl<float, 3>(h, sds, h->K32.lu, h->K32.sinv);
+    else factor_impl<double, 3>(h, sds, h->K64.lu, h->K64.sinv);
+  }
+}
+
+template <typename T, int DIM, int MODE>
+static void spmv(hf_mesh* h, const T* dg, const T* off, const T* x, T* y, const int* skip) {
+  int eb = (int)((h->ne + 127) / 128);
+  int pb = (int)((h->np + 127) / 128);
+  k_spmv<T, DIM, MODE><<<eb + pb, 128, 0, h->stream>>>(h->d, dg, off, x, y, eb, skip);
+}
+
+template <typename T, int DIM>
+static void precond(hf_mesh* h, const Krylov<T>& K, const T* rin, const double* scale, T* vout, T* z,
+                    const int* skip) {
+  using S = Shape<DIM>;
+  size_t sm = ((size_t)h->G * S::ned + 4 * 32) * sizeof(T);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_ilu_apply<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  k_ilu_apply<T, DIM><<<h->d.nsd, 128, sm, h->stream>>>(h->d, K.lu, rin, scale, vout, z, skip);
+  if (h->np > 0)
+    k_prec_p<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, rin, scale, vout, K.sinv, z, skip);
+}
+
+// one GMRES(m) cycle on x (V[0] and gs already set by k_residual_start)
+template <typename T, int DIM>
+static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest) {
+  GmresState* gs = h->d_gs;
+  const int* done = &gs->done;
+  long long N = h->N;
+  int rb = h->red_blocks;
+  int* cnt = h->d_count + 4;
+  for (int j = 0; j < mrest; ++j) {
+    T* vj = K.V + (long long)j * K.ldv;
+    prof_begin(h, PK_PREC);
+    precond<T, DIM>(h, K, vj, nullptr, nullptr, K.z, done);
+    prof_end(h);
+    prof_begin(h, PK_SPMV);
+    spmv<T, DIM, 0>(h, dg, off, K.z, K.w, done);
+    prof_end(h);
+    prof_begin(h, PK_ORTH);
+    k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs);
+    k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest);
+    k_scale_into<T><<<rb, RB, 0, h->stream>>>(K.w, K.V + (long long)(j + 1) * K.ldv, N, &gs->inv_h, done);
+    prof_end(h);
+  }
+  k_backsolve<<<1, 32, 0, h->stream>>>(gs);
+  k_combine<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, N, gs, K.u);
+  precond<T, DIM>(h, K, K.u, nullptr, nullptr, K.z, nullptr);
+  k_axpy<T><<<rb, RB, 0, h->stream>>>(K.x, K.z, N);
+}
+
+template <typename T, int DIM>
+static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest, cudaGraphExec_t* gexec) {
+  if (!h->opts.use_graphs) {
+    gmres_cycle<T, DIM>(h, K, dg, off, mrest);
+    return HF_OK;
+  }
+  if (!*gexec) {
+    cudaGraph_t g;
+    cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return check_cuda(h, e, "cudaStreamBeginCapture");
+    bool pon = h->prof.on;
+    h->prof.on = false;
+    gmres_cycle<T, DIM>(h, K, dg, off, mrest);
+    h->prof.on = pon;
+    e = cudaStreamEndCapture(h->stream, &g);
+    if (e != cudaSuccess) return check_cuda(h, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return check_cuda(h, e, "cudaGraphInstantiate");
+  }
+  return check_cuda(h, cudaGraphLaunch(*gexec, h->stream), "cudaGraphLaunch");
+}
+
+struct CycleInfo {
+  double beta;
+  int iters;
+  int done;
+};
+
+static hf_status read_gs(hf_mesh* h, CycleInfo* ci) {
+  GmresState tmp;
+  cudaError_t e = cudaMemcpyAsync(&tmp, h->d_gs, sizeof(GmresState), cudaMemcpyDeviceToHost, h->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+  prof_flush(h);
+  if (e != cudaSuccess) return check_cuda(h, e, "gmres state read");
+  ci->beta = tmp.beta;
+  ci->iters = tmp.iters;
+  ci->done = tmp.done;
+  return HF_OK;
+}
+
+template <int DIM>
+static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_report* rep) {
+  const hf_solver_opts& o = h->opts;
+  long long N = h->N;
+  int rb = h->red_blocks;
+  int* cnt = h->d_count + 4;
+  int mrest = std::max(1, std::min(30, o.restart));
+  // ||b||
+  k_norm2<double><<<rb, RB, 0, h->stream>>>(b, N, h->d_partial, cnt, h->d_red);
+  double bn2 = 0.0;
+  cudaMemcpyAsync(&bn2, h->d_red, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  hf_status st = check_cuda(h, cudaStreamSynchronize(h->stream), "norm");
+  if (st) return st;
+  double bnorm = sqrt(bn2);
+  if (!std::isfinite(bnorm)) return set_error(h, HF_ERR_NONFINITE, "right-hand side is not finite");
+  double tol = o.rtol * bnorm;
+  int total = 0, refinements = 0;
+  double rnorm = bnorm;
+  k_fill<double><<<rb, RB, 0, h->stream>>>(x, N, 0.0);
+  if (bnorm == 0.0) {
+    if (rep) {
+      rep->gmres_iters = 0;
+      rep->lin_res = 0.0;
+      rep->lin_converged = 1;
+      rep->refinements = 0;
+    }
+    return HF_OK;
+  }
+  if (o.precision == HF_PREC_FP64) {
+    Krylov<double>& K = h->K64;
+    k_fill<double><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0);
+    for (;;) {
+      spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, K.x, K.w, nullptr);
+      k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, K.w, K.V, N, h->d_partial, cnt, h->d_gs, tol);
+      k_scale_into<double><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr);
+      CycleInfo ci;
+      cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
+      if ((st = read_gs(h, &ci))) break;
+      rnorm = ci.beta;
+      if (!std::isfinite(rnorm)) {
+        st = set_error(h, HF_ERR_NONFINITE, "GMRES residual is not finite");
+        break;
+      }
+      if (rnorm <= tol || total >= o.max_iters) break;
+      if ((st = run_cycle<double, DIM>(h, K, h->J64.dg, h->J64.off, mrest, &h->graph64))) break;
+      if ((st = read_gs(h, &ci))) break;
+      total += ci.iters;
+    }
+    cudaMemcpyAsync(x, K.x, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  } else {
+    Krylov<float>& K = h->K32;
+    if (!h->j32_valid) convert_j32(h);
+    double* r = h->r64;
+    cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    for (;;) {
+      k_norm2<double><<<rb, RB, 0, h->stream>>>(r, N, h->d_partial, cnt, h->d_red);
+      double rn2 = 0.0;
+      cudaMemcpyAsync(&rn2, h->d_red, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+      if ((st = check_cuda(h, cudaStreamSynchronize(h->stream), "norm"))) break;
+      rnorm = sqrt(rn2);
+      if (!std::isfinite(rnorm)) {
+        st = set_error(h, HF_ERR_NONFINITE, "refinement residual is not finite");
+        break;
+      }
+      if (rnorm <= tol || total >= o.max_iters) break;
+      k_demote_scaled<<<rb, RB, 0, h->stream>>>(r, K.b, N, h->d_red);
+      k_fill<float><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0f);
+      k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs,
+                                                        o.inner_rtol);
+      k_scale_into<float><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr);
+      cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
+      if ((st = run_cycle<float, DIM>(h, K, h->J32.dg, h->J32.off, mrest, &h->graph32))) break;
+      CycleInfo ci;
+      if ((st = read_gs(h, &ci))) break;
+      total += ci.iters;
+      refinements += 1;
+      k_promote_axpy<<<rb, RB, 0, h->stream>>>(x, K.x, N, h->d_red);
+      prof_begin(h, PK_SPMV64);
+      spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, x, h->tmp64, nullptr);
+      prof_end(h);
+      k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, h->tmp64, r, N, h->d_partial, cnt, h->d_gs + 0, 0.0);
+      if (ci.iters == 0) break;
+    }
+  }
+  if (rep) {
+    rep->gmres_iters = total;
+    rep->refinements = refinements;
+    rep->lin_res = rnorm / bnorm;
+    rep->lin_converged = rnorm <= tol;
+  }
+  return st;
+}
+
+hf_status linear_solve(hf_mesh* h, const double* b, double* x, hf_newton_report* rep) {
+  return h->dim == 2 ? solve_impl<2>(h, b, x, rep) : solve_impl<3>(h, b, x, rep);
+}
+
+hf_status residual(hf_mesh* h, const double* X, double* R) {
+  prof_begin(h, PK_ASSEMBLY);
+  if (h->dim == 2) spmv<double, 2, 1>(h, h->J64.dg, h->J64.off, X, R, nullptr);
+  else spmv<double, 3, 1>(h, h->J64.dg, h->J64.off, X, R, nullptr);
+  prof_end(h);
+  return HF_OK;
+}
+
+hf_status apply_jacobian(hf_mesh* h, const double* x, double* y) {
+  if (h->dim == 2) spmv<double, 2, 0>(h, h->J64.dg, h->J64.off, x, y, nullptr);
+  else spmv<double, 3, 0>(h, h->J64.dg, h->J64.off, x, y, nullptr);
+  return HF_OK;
+}
+
+double device_norm2(hf_mesh* h, const double* v, long long n) {
+  k_norm2<double><<<h->red_blocks, RB, 0, h->stream>>>(v, n, h->d_partial, h->d_count + 4, h->d_red);
+  double r = 0.0;
+  cudaMemcpyAsync(&r, h->d_red, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  return r;
+}
+
+hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]) {
+  prof_begin(h, PK_UPDATE);
+  k_newton_update<<<h->red_blocks, RB, 0, h->stream>>>(h->d, h->X, Dx, h->d_partial, h->d_count + 4, h->d_red);
+  prof_end(h);
+  cudaMemcpyAsync(out, h->d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+  hf_status s = check_cuda(h, cudaStreamSynchronize(h->stream), "newton update");
+  prof_flush(h);
+  return s;
+}
+
+void launch_neg(hf_mesh* h, const double* a, double* b) {
+  k_neg<<<h->red_blocks, RB, 0, h->stream>>>(a, b, h->N);
+}
+
+void launch_precond64(hf_mesh* h, const double* r, double* z) {
+  if (h->opts.precision == HF_PREC_MIXED) {
+    // the FP32 factor applied to an FP64 vector
+    k_d2f<<<h->red_blocks, RB, 0, h->stream>>>(r, h->K32.b, h->N);
+    if (h->dim == 2) precond<float, 2>(h, h->K32, h->K32.b, nullptr, nullptr, h->K32.z, nullptr);
+    else precond<float, 3>(h, h->K32, h->K32.b, nullptr, nullptr, h->K32.z, nullptr);
+    k_f2d<<<h->red_blocks, RB, 0, h->stream>>>(h->K32.z, z, h->N);
+  } else {
+    if (h->dim == 2) precond<double, 2>(h, h->K64, r, nullptr, nullptr, z, nullptr);
+    else precond<double, 3>(h, h->K64, r, nullptr, nullptr, z, nullptr);
+  }
+}
+
+}  // namespace hfk

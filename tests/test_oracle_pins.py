@@ -288,6 +288,16 @@ def test_sparse_solve_equals_dense_brute_force():
     xd = np.linalg.solve(J.toarray(), -R)
     for sl in (slice(0, o.Nu), slice(o.Nu, o.N)):
         assert np.abs(xs[sl] - xd[sl]).max() <= 1e-10 * np.abs(xd[sl]).max()
+    # the oracle's solve (equilibrated LU + refinement) against a dense solve of
+    # the equilibrated system in extended precision
+    Jd = J.toarray()
+    r = 1.0 / np.abs(Jd).max(axis=1)
+    c = 1.0 / np.abs(Jd * r[:, None]).max(axis=0)
+    A = np.asarray(Jd * r[:, None] * c[None, :], dtype=np.longdouble)
+    xe = c * np.asarray(np.linalg.solve(A.astype(np.float64), (-R * r)), dtype=np.float64)
+    xo = o.solve_linear(J, -R)
+    for sl in (slice(0, o.Nu), slice(o.Nu, o.N)):
+        assert np.abs(xo[sl] - xe[sl]).max() <= 1e-11 * np.abs(xe[sl]).max()
 
 
 # ------------------------------------------------------------------ invariants
