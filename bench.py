@@ -1,0 +1,391 @@
+#!/usr/bin/env python3
+"""Newton iterations per second of the fully-coupled hydraulic-fracture step
+on one GB300 (assembly + ILU(0) block-Jacobi GMRES), through the C ABI.
+
+Workload: 3D penny-shaped fracture, cube of 50 m side split into 18^3 cubes of
+six P2 tetrahedra (34,992 elements, 1,100,305 unknowns), point injection at
+the centre of z = 0, every interior facet crackable.  A step is one Newton
+iteration of the time-stepping loop (Newton until converged, fracture
+criterion, end of step); each linear solve is driven to a relative residual of
+1e-8.  The headline runs the FP32-inner / FP64-refinement path; the FP64 path
+is timed beside it on the same state.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Under torchrun each rank solves its own replica of the workload (the method's
+instances are independent; nothing is exchanged), rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "Newton iters/s (assembly+GMRES) at ~1M DOF, FP64 vs mixed @1e-8; p99 latency"
+UNIT = "Newton it/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def dist_env():
+    return int(os.environ.get("RANK", 0)), int(os.environ.get("WORLD_SIZE", 1)), int(os.environ.get("LOCAL_RANK", 0))
+
+
+def workload(name):
+    from hf_inputs import c3_penny, kgd_2d, penny_3d
+    if name == "c3":
+        return c3_penny()
+    if name == "small3d":
+        return penny_3d(n=6, name="penny3d_n6")
+    if name == "c1":
+        return kgd_2d(n=44, name="c1_kgd2d_n44")
+    raise ValueError(name)
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            return float(d["hbm_gbs"]), "measured"
+        except Exception:
+            pass
+    return FALLBACK_HBM_GBS, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        self.f.flush()
+        rows = [r.split(",") for r in open(self.f.name).read().strip().splitlines() if r.strip()]
+        sm = [float(r[1]) for r in rows if len(r) > 8 and r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if len(r) > 8 and r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            if len(r) > 8:
+                for n, v in zip(names, r[5:9]):
+                    if "Active" in v and "Not" not in v:
+                        reasons.add(n)
+        os.unlink(self.f.name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def make_problem(wl, precision, stream_ptr, G, restart):
+    from paper_1911_10275_gb300 import HFMesh
+    g = HFMesh.from_mesh(wl.mesh, stream=stream_ptr)
+    inj, wts = wl.injection()
+    g.hf_set_material(wl.E, wl.nu, wl.sigma_c, wl.delta_c, wl.b_stab)
+    g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.mesh.length)
+    g.hf_set_solver(precision=precision, restart=restart, rtol=1e-8, inner_rtol=1e-3, max_iters=20000,
+                    jacobi_block=G, newton_tol=1e-8)
+    return g
+
+
+class NewtonLoop:
+    """Time stepping as the paper drives it: Newton to convergence (or a cap),
+    the fracture criterion, re-Newton if it switched facets, end of step."""
+
+    def __init__(self, g, newton_cap=8):
+        self.g = g
+        self.cap = newton_cap
+        self.it_in_step = 0
+        self.reports = []
+        self.latencies = []
+
+    def step(self):
+        t0 = time.perf_counter()
+        rep = self.g.hf_newton_step()
+        self.reports.append(rep)
+        self.it_in_step += 1
+        if rep["converged"] or self.it_in_step >= self.cap:
+            new_alpha = self.g.hf_check_fracture_criterion()
+            if new_alpha == 0 or self.it_in_step >= 3 * self.cap:
+                self.g.hf_accept_step()
+                self.it_in_step = 0
+        self.latencies.append(time.perf_counter() - t0)
+        return rep
+
+
+def algorithmic_bytes(stats, dim, elt):
+    """Bytes one launch must move at minimum (stated in the design doc):
+    SpMV: every stored element-block value once, x and y once, neighbour ids;
+    preconditioner: diagonal inverses plus in-subdomain L/U blocks once, its
+    input and output vector once."""
+    ned = 30 if dim == 3 else 12
+    nfr = 18 if dim == 3 else 6
+    ne = stats["elements"]
+    N = ne * ned + stats["n_p"]
+    spmv_vals = ne * ned * ned + stats["interior_slots"] * ned * nfr
+    prec_vals = ne * ned * ned + stats["subdomain_slots"] * ned * nfr
+    return {"spmv": spmv_vals * elt + 2 * N * elt + ne * (dim + 1) * 4,
+            "precond": prec_vals * elt + 2 * N * elt + ne * 8}
+
+
+def traffic_from_profiles(kernel):
+    p = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(p):
+        return None
+    try:
+        d = json.load(open(p))
+        return d.get(kernel)
+    except Exception:
+        return None
+
+
+def run_ours(args):
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    dev = torch.device("cuda", local if world > 1 else 0)
+    torch.cuda.set_device(dev)
+    wl = workload(args.config)
+    stream = torch.cuda.Stream(device=dev)
+    prec = "mixed" if args.precision == "mixed" else "fp64"
+    g = make_problem(wl, prec, stream.cuda_stream, args.jacobi_block, args.restart)
+    U, P, al, be = wl.seed()
+    g.hf_set_state(U, P, al, be)
+    loop = NewtonLoop(g)
+    for _ in range(args.warmup):
+        loop.step()
+    stats = g.hf_get_stats()
+    launches0 = stats["kernel_launches"]
+    g.hf_set_profiling(True)
+    loop.reports.clear()
+    loop.latencies.clear()
+    sampler = ClockSampler(local)
+    sampler.start()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        loop.step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = sampler.stop()
+    ms = ev0.elapsed_time(ev1)
+    ktimes = g.hf_get_kernel_times()
+    g.hf_set_profiling(False)
+    stats = g.hf_get_stats()
+    launches = stats["kernel_launches"] - launches0
+    reports = list(loop.reports)
+    lat = sorted(loop.latencies)
+    if world > 1:
+        t = torch.tensor([ms], dtype=torch.float64, device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms = float(t.item())
+    value = args.steps * world / (ms / 1000.0)
+
+    # FP64 beside it on the same starting state (fewer steps)
+    fp64 = None
+    if args.precision == "mixed" and args.fp64_steps > 0:
+        g.hf_set_solver(precision="fp64", restart=args.restart, rtol=1e-8, max_iters=20000,
+                        jacobi_block=args.jacobi_block, newton_tol=1e-8)
+        g.hf_set_state(U, P, al, be)
+        l64 = NewtonLoop(g)
+        for _ in range(min(args.warmup, 2)):
+            l64.step()
+        l64.reports.clear()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.fp64_steps):
+            l64.step()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = e0.elapsed_time(e1)
+        fp64 = {"value": args.fp64_steps / (ms64 / 1000.0), "unit": UNIT, "steps": args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps,
+                "gmres_iters_per_newton": float(np.mean([r["gmres_iters"] for r in l64.reports]))}
+        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=20000,
+                        jacobi_block=args.jacobi_block, newton_tol=1e-8)
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if args.e2e_steps > 0:
+        g.hf_set_state(U, P, al, be)
+        Uh, Ph, ah, bh, wh, th = g.hf_get_state()
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        Uh, Ph, ah, bh, wh = pin(Uh), pin(Ph), pin(ah), pin(bh), pin(wh)
+        h2d = Uh.nbytes + Ph.nbytes + ah.nbytes + bh.nbytes + wh.nbytes
+        d2h = 0
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g.hf_set_state(Uh, Ph, ah, bh, wh, th)
+            g.hf_newton_step()
+            out = g.hf_get_state()
+            Uh[:], Ph[:] = out[0], out[1]
+            wh[:] = out[4]
+            d2h = sum(x.nbytes for x in out[:5])
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        e2e = {"value": args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h)}
+
+    # roofline of the dominant kernel class, from the events of the timed region
+    elt = 4 if prec == "mixed" else 8
+    algo = algorithmic_bytes(stats, wl.mesh.dim, elt)
+    cand = {k: ktimes[k] for k in ("spmv", "precond")}
+    dom = max(cand, key=lambda k: cand[k][0])
+    kms, kl = cand[dom]
+    peak, peak_src = peaks()
+    achieved = algo[dom] / (kms / kl / 1000.0) / 1e9 if kl else 0.0
+    kname = {"spmv": f"k_spmv<{'float' if elt == 4 else 'double'},3,0>",
+             "precond": f"k_ilu_apply<{'float' if elt == 4 else 'double'},3>"}[dom]
+    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src,
+                "algorithmic_bytes_per_launch": int(algo[dom]), "launches": kl,
+                "avg_launch_us": 1000.0 * kms / kl if kl else None,
+                "traffic": traffic_from_profiles(kname)}
+    total_ms = sum(v[0] for v in ktimes.values())
+    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in ktimes.items() if v[1]}
+
+    gmres = [r["gmres_iters"] for r in reports]
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32-inner/f64-refinement" if prec == "mixed" else "f64",
+        "data": "synthetic (seeded structured P2 mesh and seed crack)",
+        "config": {"workload": wl.name, "dofs": int(g.N), "elements": int(wl.mesh.n_elems),
+                   "precision": prec, "gmres_rtol": 1e-8, "restart": args.restart,
+                   "jacobi_block": args.jacobi_block, "parallelism": f"replicas x{world}",
+                   "l2": "working set larger than L2 (matrix + factor %.2f GB per replica)" %
+                         (2 * algo["spmv"] / 1e9)},
+        "fp64": fp64,
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "kernel_ms": breakdown,
+        "kernel_ms_total_share_of_step": total_ms / ms if ms else None,
+        "gmres_iters_per_newton": float(np.mean(gmres)) if gmres else None,
+        "newton_latency_ms": {"p50": 1000 * lat[len(lat) // 2], "p99": 1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
+        if lat else None,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and args.cpu_baseline:
+        out["cpu_baseline"] = oracle_baseline(wl, args.cpu_budget)
+    g.close()
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(out))
+
+
+def oracle_baseline(wl, budget_s):
+    """The oracle as it stands on the host cores, on a bounded sample of the
+    same workload: the residual and Jacobian terms of a sample of elements and
+    interior facets, scaled to the whole mesh.  The oracle's sparse direct
+    solve cannot run at this size (fill-in), so the figure excludes the linear
+    solve and is an upper bound on the oracle's Newton rate."""
+    from oracle import Oracle, Params
+    inj, wts = wl.injection()
+    t0 = time.perf_counter()
+    prm = Params(E=wl.E, nu=wl.nu, sigma_c=wl.sigma_c, delta_c=wl.delta_c, b_stab=wl.b_stab, mu=wl.mu, Q0=wl.Q0,
+                 inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=wl.delta_f, dt=wl.dt, L_ref=wl.mesh.length)
+    o = Oracle(wl.mesh, prm)
+    U, P, al, be = wl.seed()
+    o.set_state(U, P, al, be)
+    t_setup = time.perf_counter() - t0
+    rng = np.random.default_rng(0)
+    interior = np.nonzero(wl.mesh.face_elems[:, 1] >= 0)[0]
+    n_e = n_f = 0
+    t_e = t_f = 0.0
+    deadline = time.perf_counter() + budget_s
+    while time.perf_counter() < deadline:
+        e = int(rng.integers(0, o.ne))
+        t1 = time.perf_counter()
+        o.element_stiffness(e)
+        t_e += time.perf_counter() - t1
+        n_e += 1
+        f = int(interior[rng.integers(0, interior.size)])
+        t1 = time.perf_counter()
+        o.intact_blocks(f)
+        t_f += time.perf_counter() - t1
+        n_f += 1
+    t_full = t_e / n_e * o.ne + t_f / n_f * interior.size
+    return {"value": 1.0 / t_full, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"oracle assembly of {n_e} random elements and {n_f} random interior facets of "
+                      f"{wl.name} ({o.ne} elements, {interior.size} interior facets), scaled to the full "
+                      f"mesh ({t_full:.1f} s per Newton iteration); sparse direct solve excluded "
+                      f"(infeasible at this size), so an upper bound; set-up {t_setup:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    wl = workload(args.config)
+    base = oracle_baseline(wl, args.cpu_budget)
+    out = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1000.0 / base["value"], "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
+           "data": "synthetic (seeded structured P2 mesh and seed crack)",
+           "config": {"workload": wl.name, "precision": "fp64 oracle"},
+           "cpu_baseline": base,
+           "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c3")
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--jacobi-block", dest="jacobi_block", type=int, default=32)
+    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--fp64-steps", dest="fp64_steps", type=int, default=3)
+    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
+    ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -263,10 +263,10 @@ class HFMesh:
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 
     def hf_get_stats(self):
-        st = np.zeros(8, np.int64)
+        st = np.zeros(16, np.int64)
         self._check(self.lib.hf_get_stats(self.h, _ptr(st, C.c_int64)))
         keys = ["elements", "interior_slots", "subdomain_slots", "levels_max", "subdomains", "nl_faces",
-                "n_p", "faces"]
+                "n_p", "faces", "kernel_launches"]
         return dict(zip(keys, (int(x) for x in st)))
 
     def hf_solve_linear(self, rhs):

@@ -16,6 +16,13 @@
 using namespace hfk;
 
 namespace hfk {
+long long& launch_counter() {
+  static long long n = 0;
+  return n;
+}
+}  // namespace hfk
+
+namespace hfk {
 void launch_neg(hf_mesh* h, const double* a, double* b);
 void launch_precond64(hf_mesh* h, const double* r, double* z);
 }
@@ -1004,6 +1011,8 @@ hf_status hf_get_stats(const hf_mesh* h, int64_t* st) {
   st[5] = h->d.n_nl;
   st[6] = h->np;
   st[7] = h->nf;
+  st[8] = launch_counter();
+  for (int i = 9; i < 16; ++i) st[i] = 0;
   return HF_OK;
 }
 

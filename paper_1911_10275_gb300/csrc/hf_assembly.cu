@@ -507,38 +507,38 @@ __global__ void k_fluid_scale(DevMesh m, int enabled, double L_ref) {
 // ---------------------------------------------------------------- launchers
 template <int DIM>
 void launch_geometry(const DevMesh& m, cudaStream_t st) {
-  k_elem_geometry<DIM><<<(m.ne + 127) / 128, 128, 0, st>>>(m);
-  k_face_geometry<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m);
+  { note_launch(); k_elem_geometry<DIM><<<(m.ne + 127) / 128, 128, 0, st>>>(m); }
+  { note_launch(); k_face_geometry<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m); }
 }
 template <int DIM>
 void launch_build_rows(const DevMesh& m, const Quad& q, const int* elist, int n, double* dg, double* off,
                        cudaStream_t st) {
-  if (n > 0) k_build_rows<DIM><<<(n + 3) / 4, 128, 0, st>>>(m, q, elist, n, dg, off);
+  if (n > 0) { note_launch(); k_build_rows<DIM><<<(n + 3) / 4, 128, 0, st>>>(m, q, elist, n, dg, off); }
 }
 template <int DIM>
 void launch_neumann(const DevMesh& m, const Quad& q, const double* ftrac, const signed char* fneu,
                     cudaStream_t st) {
-  k_neumann<DIM><<<(m.ne + 127) / 128, 128, 0, st>>>(m, q, ftrac, fneu);
+  { note_launch(); k_neumann<DIM><<<(m.ne + 127) / 128, 128, 0, st>>>(m, q, ftrac, fneu); }
 }
 template <int DIM>
 void launch_face_nl(const DevMesh& m, const Quad& q, const double* X, cudaStream_t st) {
-  if (m.n_nl > 0) k_face_nl<DIM><<<(m.n_nl + 3) / 4, 128, 0, st>>>(m, q, X);
+  if (m.n_nl > 0) { note_launch(); k_face_nl<DIM><<<(m.n_nl + 3) / 4, 128, 0, st>>>(m, q, X); }
 }
 template <int DIM>
 void launch_criterion(const DevMesh& m, const Quad& q, const double* X, double* tmax, int* n_new,
                       cudaStream_t st) {
-  k_criterion<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m, q, X, tmax, n_new);
+  { note_launch(); k_criterion<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m, q, X, tmax, n_new); }
 }
 template <int DIM>
 void launch_openings(const DevMesh& m, const double* X, double* w, cudaStream_t st) {
-  k_face_openings<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m, X, w);
+  { note_launch(); k_face_openings<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m, X, w); }
 }
 template <int DIM>
 void launch_accept(const DevMesh& m, const Quad& q, const double* X, int* n_new, cudaStream_t st) {
-  k_accept<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m, q, X, n_new);
+  { note_launch(); k_accept<DIM><<<(m.nf + 127) / 128, 128, 0, st>>>(m, q, X, n_new); }
 }
 void launch_fluid_scale(const DevMesh& m, int enabled, double L_ref, cudaStream_t st) {
-  k_fluid_scale<<<1, 1024, 0, st>>>(m, enabled, L_ref);
+  { note_launch(); k_fluid_scale<<<1, 1024, 0, st>>>(m, enabled, L_ref); }
 }
 
 #define HF_INST(DIM)                                                                             \

@@ -24,6 +24,10 @@
 
 namespace hfk {
 
+// process-wide count of kernel launches issued by the library (host side)
+long long& launch_counter();
+inline void note_launch() { ++launch_counter(); }
+
 constexpr int MAXFN = 6;     // face nodes of a P2 facet (3D)
 constexpr int MAXNED = 30;   // unknowns of a P2 tetrahedron
 constexpr int MAXNQ = 25;    // nonlinear facet rule size (3D)

@@ -117,32 +117,34 @@ __device__ void pressure_row(const DevMesh& m, int g, const T* __restrict__ x, T
   y[m.nu + g] = (T)(c * acc);
 }
 
-template <typename T, int DIM, int MODE>
-__global__ void __launch_bounds__(128) k_spmv(DevMesh m, const T* __restrict__ dg, const T* __restrict__ off,
-                                              const T* __restrict__ x, T* __restrict__ y, int eblocks,
-                                              const int* skip) {
+// Node groups: the element's nodes are split into SPMV_P(DIM) groups of two
+// nodes; warp g of a CTA owns the 2*DIM rows of group g for 32 consecutive
+// elements (lane = element).  Every matrix value is read exactly once, with
+// the element index fastest, so each warp load is one contiguous 128/256-byte
+// segment.  The group's rows are compile-time, so accumulators stay in
+// registers.
+template <int DIM> struct SpmvGroups {
+  static constexpr int P = Shape<DIM>::nen / 2;   // 3 (2D) or 5 (3D) warps per CTA
+  static constexpr int R = 2 * DIM;               // rows per group
+};
+
+template <typename T, int DIM, int MODE, int GRP>
+__device__ __forceinline__ void spmv_group(const DevMesh& m, const T* __restrict__ dg, const T* __restrict__ off,
+                                           const T* __restrict__ x, T* __restrict__ y, int e) {
   using S = Shape<DIM>;
-  constexpr int NED = S::ned, NFR = S::nfr;
-  if (skip && *skip) return;
-  if ((int)blockIdx.x >= eblocks) {
-    int g = (blockIdx.x - eblocks) * blockDim.x + threadIdx.x;
-    if (g < m.np) pressure_row<T, DIM, MODE>(m, g, x, y);
-    return;
-  }
-  int e = blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= m.ne) return;
+  constexpr int NED = S::ned, NFR = S::nfr, R = SpmvGroups<DIM>::R, R0 = GRP * R;
   const long long ne = m.ne;
-  T acc[NED];
+  T acc[R];
 #pragma unroll
-  for (int r = 0; r < NED; ++r) acc[r] = (T)0;
+  for (int r = 0; r < R; ++r) acc[r] = (T)0;
   const T* xe = x + (long long)e * NED;
   const T* dge = dg + e;
-#pragma unroll 2
+#pragma unroll 5
   for (int c = 0; c < NED; ++c) {
     T xc = xe[c];
-    const T* col = dge + (long long)c * NED * ne;
+    const T* col = dge + ((long long)c * NED + R0) * ne;
 #pragma unroll
-    for (int r = 0; r < NED; ++r) acc[r] += ld(col + r * ne) * xc;
+    for (int r = 0; r < R; ++r) acc[r] += ld(col + r * ne) * xc;
   }
 #pragma unroll
   for (int j = 0; j < DIM + 1; ++j) {
@@ -150,27 +152,59 @@ __global__ void __launch_bounds__(128) k_spmv(DevMesh m, const T* __restrict__ d
     if (nb >= 0) {
       const T* xn = x + (long long)nb * NED;
       const T* ob = off + (long long)j * NED * NFR * ne + e;
-#pragma unroll 2
+#pragma unroll 6
       for (int c = 0; c < NED; ++c) {
         T xc = xn[c];
         const T* col = ob + (long long)c * NFR * ne;
 #pragma unroll
-        for (int rr = 0; rr < NFR; ++rr)
-          acc[face_node<DIM>(j, rr / DIM) * DIM + rr % DIM] += ld(col + rr * ne) * xc;
+        for (int rr = 0; rr < NFR; ++rr) {
+          constexpr int dummy = 0;
+          (void)dummy;
+          const int node = face_node<DIM>(j, rr / DIM);
+          if (node / 2 == GRP) acc[(node % 2) * DIM + rr % DIM] += ld(col + rr * ne) * xc;
+        }
       }
     }
   }
-  T* ye = y + (long long)e * NED;
+  T* ye = y + (long long)e * NED + R0;
   if (MODE == 1) {
     unsigned dm = m.dirmask[e];
 #pragma unroll
-    for (int r = 0; r < NED; ++r)
-      acc[r] -= (T)(((dm >> r) & 1u) ? m.ubar[(long long)e * NED + r] : m.fext[(long long)e * NED + r]);
+    for (int r = 0; r < R; ++r)
+      acc[r] -= (T)(((dm >> (R0 + r)) & 1u) ? m.ubar[(long long)e * NED + R0 + r] : m.fext[(long long)e * NED + R0 + r]);
   }
 #pragma unroll
-  for (int r = 0; r < NED; ++r) ye[r] = acc[r];
-  unsigned nlm = m.nlmask[e];
-  if (nlm) add_nl_terms<T, DIM, MODE>(m, e, nlm, x, y);
+  for (int r = 0; r < R; ++r) ye[r] = acc[r];
+}
+
+template <typename T, int DIM, int MODE>
+__global__ void __launch_bounds__(32 * SpmvGroups<DIM>::P) k_spmv(DevMesh m, const T* __restrict__ dg,
+                                                                   const T* __restrict__ off, const T* __restrict__ x,
+                                                                   T* __restrict__ y, int eblocks, const int* skip) {
+  if (skip && *skip) return;
+  if ((int)blockIdx.x >= eblocks) {
+    int g = (blockIdx.x - eblocks) * blockDim.x + threadIdx.x;
+    if (g < m.np) pressure_row<T, DIM, MODE>(m, g, x, y);
+    return;
+  }
+  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int e = blockIdx.x * 32 + lane;
+  bool live = e < m.ne;
+  if (live) {
+    switch (warp) {
+      case 0: spmv_group<T, DIM, MODE, 0>(m, dg, off, x, y, e); break;
+      case 1: spmv_group<T, DIM, MODE, 1>(m, dg, off, x, y, e); break;
+      case 2: spmv_group<T, DIM, MODE, 2>(m, dg, off, x, y, e); break;
+      case 3: if (DIM == 3) spmv_group<T, DIM, MODE, 3>(m, dg, off, x, y, e); break;
+      case 4: if (DIM == 3) spmv_group<T, DIM, MODE, 4>(m, dg, off, x, y, e); break;
+    }
+  }
+  // facet terms of cohesive and fluid facets touch rows of every group
+  __syncthreads();
+  if (warp == 0 && live) {
+    unsigned nlm = m.nlmask[e];
+    if (nlm) add_nl_terms<T, DIM, MODE>(m, e, nlm, x, y);
+  }
 }
 
 // ------------------------------------------------------------------ ILU(0)
@@ -447,7 +481,7 @@ __global__ void __launch_bounds__(128) k_ilu_apply(DevMesh m, const T* __restric
         const T* blk = rec + NED * NED + j * NED * NFR;
         T dot = (T)0;
         if (lane < NFR) {
-#pragma unroll 6
+#pragma unroll
           for (int c = 0; c < NED; ++c) dot += blk[c * NFR + lane] * ys[lk * NED + c];
         }
         __syncwarp();
@@ -473,7 +507,7 @@ __global__ void __launch_bounds__(128) k_ilu_apply(DevMesh m, const T* __restric
         const T* blk = rec + NED * NED + j * NED * NFR;
         T dot = (T)0;
         if (lane < NFR) {
-#pragma unroll 6
+#pragma unroll
           for (int c = 0; c < NED; ++c) dot += blk[c * NFR + lane] * ys[lk * NED + c];
         }
         __syncwarp();
@@ -482,7 +516,7 @@ __global__ void __launch_bounds__(128) k_ilu_apply(DevMesh m, const T* __restric
       }
       T zr = (T)0;
       if (lane < NED) {
-#pragma unroll 6
+#pragma unroll
         for (int c = 0; c < NED; ++c) zr += rec[c * NED + lane] * tmp[c];
       }
       __syncwarp();
@@ -563,11 +597,22 @@ __device__ bool block_partial_last(double v, double* partial, int* counter) {
   return last;
 }
 
-__device__ double sum_partials(const double* partial, int n) {
-  const volatile double* p = partial;
+// sum of n partials written by other blocks (visible after their fence and
+// the ticket atomic), reduced by the whole block in a fixed order; the result
+// is returned to every thread
+__device__ double block_sum_partials(const double* partial, int n, int stride, int col) {
+  __shared__ double sm[RB / 32];
   double s = 0.0;
-  for (int b = 0; b < n; ++b) s += p[b];
-  return s;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) s += __ldcg(partial + (long long)b * stride + col);
+  s = warp_sum(s);
+  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) sm[warp] = s;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += sm[w];
+  __syncthreads();
+  return t;
 }
 
 // multi-dot: H[:, j] = V[:, 0..j]^T w
@@ -607,11 +652,9 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
   __syncthreads();
   if (last) {
-    if (threadIdx.x < ncols) {
-      const volatile double* p = partial;
-      double s = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += p[b * 32 + threadIdx.x];
-      gs->H[j * 31 + threadIdx.x] = s;
+    for (int c = 0; c < ncols; ++c) {
+      double s = block_sum_partials(partial, gridDim.x, 32, c);
+      if (threadIdx.x == 0) gs->H[j * 31 + c] = s;
     }
     if (threadIdx.x == 0) *counter = 0;
   }
@@ -636,8 +679,10 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
     w[i] = ww;
     acc += (double)ww * (double)ww;
   }
-  if (block_partial_last(acc, partial, counter) && threadIdx.x == 0) {
-    double nrm = sqrt(sum_partials(partial, gridDim.x));
+  if (!block_partial_last(acc, partial, counter)) return;
+  double nrm2 = block_sum_partials(partial, gridDim.x, 1, 0);
+  if (threadIdx.x == 0) {
+    double nrm = sqrt(nrm2);
     double* hc = gs->H + j * 31;
     for (int i = 0; i < j; ++i) {
       double a = hc[i], b = hc[i + 1];
@@ -713,8 +758,10 @@ __global__ void __launch_bounds__(RB) k_residual_start(const T* __restrict__ b, 
     r[i] = v;
     acc += (double)v * (double)v;
   }
-  if (block_partial_last(acc, partial, counter) && threadIdx.x == 0) {
-    double beta = sqrt(sum_partials(partial, gridDim.x));
+  if (!block_partial_last(acc, partial, counter)) return;
+  double b2 = block_sum_partials(partial, gridDim.x, 1, 0);
+  if (threadIdx.x == 0) {
+    double beta = sqrt(b2);
     gs->beta = beta;
     for (int i = 0; i < 31; ++i) gs->g[i] = 0.0;
     gs->g[0] = beta;
@@ -733,8 +780,10 @@ __global__ void __launch_bounds__(RB) k_norm2(const T* __restrict__ v, long long
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
     acc += (double)v[i] * (double)v[i];
-  if (block_partial_last(acc, partial, counter) && threadIdx.x == 0) {
-    *out = sum_partials(partial, gridDim.x);
+  if (!block_partial_last(acc, partial, counter)) return;
+  double tot = block_sum_partials(partial, gridDim.x, 1, 0);
+  if (threadIdx.x == 0) {
+    *out = tot;
     *counter = 0;
   }
 }
@@ -800,12 +849,11 @@ __global__ void __launch_bounds__(RB) k_newton_update(DevMesh m, double* X, cons
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
   __syncthreads();
-  if (last && threadIdx.x < 4) {
-    const volatile double* p = partial;
-    double s = 0.0;
-    for (int b = 0; b < (int)gridDim.x; ++b) s += p[b * 4 + threadIdx.x];
-    out[threadIdx.x] = s;
-    __syncwarp(0xfu);
+  if (last) {
+    for (int c = 0; c < 4; ++c) {
+      double t = block_sum_partials(partial, gridDim.x, 4, c);
+      if (threadIdx.x == 0) out[c] = t;
+    }
     if (threadIdx.x == 0) *counter = 0;
   }
 }
@@ -910,7 +958,7 @@ hf_status solver_alloc(hf_mesh* h) {
 
 void convert_j32(hf_mesh* h) {
   size_t nmat = (size_t)h->ne * (h->ned * h->ned + (h->dim + 1) * h->ned * h->nfr);
-  k_d2f<<<grid_for(nmat, 256, 152 * 16), 256, 0, h->stream>>>(h->J64.dg, h->J32.dg, nmat);
+  { note_launch(); k_d2f<<<grid_for(nmat, 256, 152 * 16), 256, 0, h->stream>>>(h->J64.dg, h->J32.dg, nmat); }
   h->j32_valid = true;
 }
 
@@ -924,9 +972,9 @@ template <typename T, int DIM> static void factor_impl(hf_mesh* h, const std::ve
     cudaMemcpyAsync(h->d_sdlist, sds.data(), sds.size() * sizeof(int), cudaMemcpyHostToDevice, h->stream);
     size_t sm = factor_smem<DIM>(sizeof(T));
     cudaFuncSetAttribute(k_ilu_factor<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_ilu_factor<T, DIM><<<(int)sds.size(), 128, sm, h->stream>>>(h->d, h->J64.dg, h->J64.off, lu, h->d_sdlist);
+    { note_launch(); k_ilu_factor<T, DIM><<<(int)sds.size(), 128, sm, h->stream>>>(h->d, h->J64.dg, h->J64.off, lu, h->d_sdlist); }
   }
-  if (h->np > 0) k_schur<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, lu, sinv);
+  if (h->np > 0) { note_launch(); k_schur<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, lu, sinv); }
 }
 
 void factor_subdomains(hf_mesh* h, const std::vector<int>& sds) {
@@ -947,9 +995,10 @@ void factor_subdomains(hf_mesh* h, const std::vector<int>& sds) {
 
 template <typename T, int DIM, int MODE>
 static void spmv(hf_mesh* h, const T* dg, const T* off, const T* x, T* y, const int* skip) {
-  int eb = (int)((h->ne + 127) / 128);
-  int pb = (int)((h->np + 127) / 128);
-  k_spmv<T, DIM, MODE><<<eb + pb, 128, 0, h->stream>>>(h->d, dg, off, x, y, eb, skip);
+  constexpr int nt = 32 * SpmvGroups<DIM>::P;
+  int eb = (int)((h->ne + 31) / 32);
+  int pb = (int)((h->np + nt - 1) / nt);
+  { note_launch(); k_spmv<T, DIM, MODE><<<eb + pb, nt, 0, h->stream>>>(h->d, dg, off, x, y, eb, skip); }
 }
 
 template <typename T, int DIM>
@@ -958,9 +1007,9 @@ static void precond(hf_mesh* h, const Krylov<T>& K, const T* rin, const double* 
   using S = Shape<DIM>;
   size_t sm = ((size_t)h->G * S::ned + 4 * 32) * sizeof(T);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_ilu_apply<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  k_ilu_apply<T, DIM><<<h->d.nsd, 128, sm, h->stream>>>(h->d, K.lu, rin, scale, vout, z, skip);
+  { note_launch(); k_ilu_apply<T, DIM><<<h->d.nsd, 128, sm, h->stream>>>(h->d, K.lu, rin, scale, vout, z, skip); }
   if (h->np > 0)
-    k_prec_p<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, rin, scale, vout, K.sinv, z, skip);
+    { note_launch(); k_prec_p<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, rin, scale, vout, K.sinv, z, skip); }
 }
 
 // one GMRES(m) cycle on x (V[0] and gs already set by k_residual_start)
@@ -980,15 +1029,15 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
     spmv<T, DIM, 0>(h, dg, off, K.z, K.w, done);
     prof_end(h);
     prof_begin(h, PK_ORTH);
-    k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs);
-    k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest);
-    k_scale_into<T><<<rb, RB, 0, h->stream>>>(K.w, K.V + (long long)(j + 1) * K.ldv, N, &gs->inv_h, done);
+    { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs); }
+    { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest); }
+    { note_launch(); k_scale_into<T><<<rb, RB, 0, h->stream>>>(K.w, K.V + (long long)(j + 1) * K.ldv, N, &gs->inv_h, done); }
     prof_end(h);
   }
-  k_backsolve<<<1, 32, 0, h->stream>>>(gs);
-  k_combine<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, N, gs, K.u);
+  { note_launch(); k_backsolve<<<1, 32, 0, h->stream>>>(gs); }
+  { note_launch(); k_combine<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, N, gs, K.u); }
   precond<T, DIM>(h, K, K.u, nullptr, nullptr, K.z, nullptr);
-  k_axpy<T><<<rb, RB, 0, h->stream>>>(K.x, K.z, N);
+  { note_launch(); k_axpy<T><<<rb, RB, 0, h->stream>>>(K.x, K.z, N); }
 }
 
 template <typename T, int DIM>
@@ -1040,7 +1089,7 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
   int* cnt = h->d_count + 4;
   int mrest = std::max(1, std::min(30, o.restart));
   // ||b||
-  k_norm2<double><<<rb, RB, 0, h->stream>>>(b, N, h->d_partial, cnt, h->d_red);
+  { note_launch(); k_norm2<double><<<rb, RB, 0, h->stream>>>(b, N, h->d_partial, cnt, h->d_red); }
   double bn2 = 0.0;
   cudaMemcpyAsync(&bn2, h->d_red, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   hf_status st = check_cuda(h, cudaStreamSynchronize(h->stream), "norm");
@@ -1050,7 +1099,7 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
   double tol = o.rtol * bnorm;
   int total = 0, refinements = 0;
   double rnorm = bnorm;
-  k_fill<double><<<rb, RB, 0, h->stream>>>(x, N, 0.0);
+  { note_launch(); k_fill<double><<<rb, RB, 0, h->stream>>>(x, N, 0.0); }
   if (bnorm == 0.0) {
     if (rep) {
       rep->gmres_iters = 0;
@@ -1062,11 +1111,11 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
   }
   if (o.precision == HF_PREC_FP64) {
     Krylov<double>& K = h->K64;
-    k_fill<double><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0);
+    { note_launch(); k_fill<double><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0); }
     for (;;) {
       spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, K.x, K.w, nullptr);
-      k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, K.w, K.V, N, h->d_partial, cnt, h->d_gs, tol);
-      k_scale_into<double><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr);
+      { note_launch(); k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, K.w, K.V, N, h->d_partial, cnt, h->d_gs, tol); }
+      { note_launch(); k_scale_into<double><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
       CycleInfo ci;
       cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
       if ((st = read_gs(h, &ci))) break;
@@ -1087,7 +1136,7 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
     double* r = h->r64;
     cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
     for (;;) {
-      k_norm2<double><<<rb, RB, 0, h->stream>>>(r, N, h->d_partial, cnt, h->d_red);
+      { note_launch(); k_norm2<double><<<rb, RB, 0, h->stream>>>(r, N, h->d_partial, cnt, h->d_red); }
       double rn2 = 0.0;
       cudaMemcpyAsync(&rn2, h->d_red, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
       if ((st = check_cuda(h, cudaStreamSynchronize(h->stream), "norm"))) break;
@@ -1097,22 +1146,21 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
         break;
       }
       if (rnorm <= tol || total >= o.max_iters) break;
-      k_demote_scaled<<<rb, RB, 0, h->stream>>>(r, K.b, N, h->d_red);
-      k_fill<float><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0f);
-      k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs,
-                                                        o.inner_rtol);
-      k_scale_into<float><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr);
+      { note_launch(); k_demote_scaled<<<rb, RB, 0, h->stream>>>(r, K.b, N, h->d_red); }
+      { note_launch(); k_fill<float><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0f); }
+      { note_launch(); k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs, o.inner_rtol); }
+      { note_launch(); k_scale_into<float><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
       cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
       if ((st = run_cycle<float, DIM>(h, K, h->J32.dg, h->J32.off, mrest, &h->graph32))) break;
       CycleInfo ci;
       if ((st = read_gs(h, &ci))) break;
       total += ci.iters;
       refinements += 1;
-      k_promote_axpy<<<rb, RB, 0, h->stream>>>(x, K.x, N, h->d_red);
+      { note_launch(); k_promote_axpy<<<rb, RB, 0, h->stream>>>(x, K.x, N, h->d_red); }
       prof_begin(h, PK_SPMV64);
       spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, x, h->tmp64, nullptr);
       prof_end(h);
-      k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, h->tmp64, r, N, h->d_partial, cnt, h->d_gs + 0, 0.0);
+      { note_launch(); k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, h->tmp64, r, N, h->d_partial, cnt, h->d_gs + 0, 0.0); }
       if (ci.iters == 0) break;
     }
   }
@@ -1144,7 +1192,7 @@ hf_status apply_jacobian(hf_mesh* h, const double* x, double* y) {
 }
 
 double device_norm2(hf_mesh* h, const double* v, long long n) {
-  k_norm2<double><<<h->red_blocks, RB, 0, h->stream>>>(v, n, h->d_partial, h->d_count + 4, h->d_red);
+  { note_launch(); k_norm2<double><<<h->red_blocks, RB, 0, h->stream>>>(v, n, h->d_partial, h->d_count + 4, h->d_red); }
   double r = 0.0;
   cudaMemcpyAsync(&r, h->d_red, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   cudaStreamSynchronize(h->stream);
@@ -1153,7 +1201,7 @@ double device_norm2(hf_mesh* h, const double* v, long long n) {
 
 hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]) {
   prof_begin(h, PK_UPDATE);
-  k_newton_update<<<h->red_blocks, RB, 0, h->stream>>>(h->d, h->X, Dx, h->d_partial, h->d_count + 4, h->d_red);
+  { note_launch(); k_newton_update<<<h->red_blocks, RB, 0, h->stream>>>(h->d, h->X, Dx, h->d_partial, h->d_count + 4, h->d_red); }
   prof_end(h);
   cudaMemcpyAsync(out, h->d_red, 4 * sizeof(double), cudaMemcpyDeviceToHost, h->stream);
   hf_status s = check_cuda(h, cudaStreamSynchronize(h->stream), "newton update");
@@ -1162,16 +1210,16 @@ hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]) {
 }
 
 void launch_neg(hf_mesh* h, const double* a, double* b) {
-  k_neg<<<h->red_blocks, RB, 0, h->stream>>>(a, b, h->N);
+  { note_launch(); k_neg<<<h->red_blocks, RB, 0, h->stream>>>(a, b, h->N); }
 }
 
 void launch_precond64(hf_mesh* h, const double* r, double* z) {
   if (h->opts.precision == HF_PREC_MIXED) {
     // the FP32 factor applied to an FP64 vector
-    k_d2f<<<h->red_blocks, RB, 0, h->stream>>>(r, h->K32.b, h->N);
+    { note_launch(); k_d2f<<<h->red_blocks, RB, 0, h->stream>>>(r, h->K32.b, h->N); }
     if (h->dim == 2) precond<float, 2>(h, h->K32, h->K32.b, nullptr, nullptr, h->K32.z, nullptr);
     else precond<float, 3>(h, h->K32, h->K32.b, nullptr, nullptr, h->K32.z, nullptr);
-    k_f2d<<<h->red_blocks, RB, 0, h->stream>>>(h->K32.z, z, h->N);
+    { note_launch(); k_f2d<<<h->red_blocks, RB, 0, h->stream>>>(h->K32.z, z, h->N); }
   } else {
     if (h->dim == 2) precond<double, 2>(h, h->K64, r, nullptr, nullptr, z, nullptr);
     else precond<double, 3>(h, h->K64, r, nullptr, nullptr, z, nullptr);
