@@ -206,6 +206,29 @@ hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
 
 const char* hf_last_error(const hf_mesh* h);
 
+/* Allocation-free Newton convergence norms.  The paper has no counterpart:
+ * this exists for callers that cannot allocate device memory (a process whose
+ * device memory belongs to a pool or arena, code that must not allocate while
+ * a CUDA graph is built around it, hosts that allocate only at start-up).
+ * Computes out[0..3] = ||dx_u||^2, ||x_u||^2, ||dx_p||^2, ||x_p||^2, the sums
+ * hf_newton_step uses for its relative increments, where the first n_u
+ * entries of the device vectors d_dx and d_x are displacements and the next
+ * n_p pressures.  d_out is device memory for 4 doubles, written on the given
+ * stream (a cudaStream_t, NULL = legacy default stream); the call does not
+ * synchronise.  It calls no cudaMalloc, cudaFree or allocating library
+ * routine: its scratch is a fixed array of 128 KiB + 256 B in the library's
+ * own device memory, which every GPU that loads the library keeps until the
+ * process exits.  n_u + n_p must not exceed 67,108,864 (the scratch holds the
+ * partial sums of at most 4096 blocks of 16,384 unknowns); larger sizes,
+ * negative sizes and null pointers return HF_ERR_INVALID_ARG.  The first call
+ * on each device looks up the scratch address with the device current (make
+ * that first call before any stream capture).  Every call shares the one
+ * scratch array and clears its counter first, so calls that overlap on the
+ * GPU (different streams, or host threads racing) give wrong results.  err
+ * (may be NULL) receives a message of at most err_len bytes. */
+hf_status hf_increment_norms_noalloc(const double* d_dx, const double* d_x, int64_t n_u, int64_t n_p,
+                                     double* d_out, void* cuda_stream, char* err, int64_t err_len);
+
 #ifdef __cplusplus
 }
 #endif

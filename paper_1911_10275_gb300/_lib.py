@@ -71,6 +71,8 @@ SIGNATURES = {
     "hf_get_kernel_times": (C.c_int, [_H, _dp, _i64p]),
     "hf_get_stats": (C.c_int, [_H, _i64p]),
     "hf_last_error": (C.c_char_p, [_H]),
+    "hf_increment_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
+                                             C.c_void_p, C.c_char_p, C.c_int64]),
 }
 KERNEL_CLASSES = ["spmv", "precond", "orth", "factor", "assembly", "spmv64", "update", "unused"]
 
