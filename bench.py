@@ -109,32 +109,77 @@ def make_problem(wl, precision, stream_ptr, G, restart):
     inj, wts = wl.injection()
     g.hf_set_material(wl.E, wl.nu, wl.sigma_c, wl.delta_c, wl.b_stab)
     g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.mesh.length)
-    g.hf_set_solver(precision=precision, restart=restart, rtol=1e-8, inner_rtol=1e-3, max_iters=20000,
+    g.hf_set_solver(precision=precision, restart=restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
                     jacobi_block=G, newton_tol=1e-8)
     return g
 
 
 class NewtonLoop:
-    """Time stepping as the paper drives it: Newton to convergence (or a cap),
-    the fracture criterion, re-Newton if it switched facets, end of step."""
+    """Time stepping as the paper drives it: Newton to convergence, the
+    fracture criterion, Newton again if it switched facets, then the end of
+    the step.  As any driver of a Newton solver does, a step whose Newton
+    iterations fail (no convergence within the cap, a linear solve that did
+    not converge, or a non-finite state) is restarted from its initial state
+    with half the time step; the step grows back after successes."""
 
-    def __init__(self, g, newton_cap=8):
+    def __init__(self, g, wl, newton_cap=8):
+        from paper_1911_10275_gb300 import HFError
+        self.HFError = HFError
         self.g = g
+        self.wl = wl
         self.cap = newton_cap
+        self.dt0 = wl.dt
+        self.dt = wl.dt
         self.it_in_step = 0
+        self.rounds = 0
         self.reports = []
         self.latencies = []
+        self.cutbacks = 0
+        self.accepted = 0
+        self.saved = g.hf_get_state()
+
+    def _set_dt(self, dt):
+        wl = self.wl
+        inj, wts = wl.injection()
+        self.dt = dt
+        self.g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, dt, 0.0, True, wl.mesh.length)
+
+    def _restart_step(self):
+        U, P, a, b, w, t = self.saved
+        self._set_dt(max(self.dt / 2, self.dt0 / 1024))
+        self.g.hf_set_state(U, P, a, b, w, t)
+        self.it_in_step = 0
+        self.rounds = 0
+        self.cutbacks += 1
 
     def step(self):
         t0 = time.perf_counter()
-        rep = self.g.hf_newton_step()
+        try:
+            rep = self.g.hf_newton_step()
+        except self.HFError:
+            rep = {"gmres_iters": 0, "converged": 0, "lin_converged": 0, "refinements": 0, "du_rel": float("nan"),
+                   "dp_rel": float("nan"), "lin_res": float("nan"), "failed": 1}
+            self._restart_step()
+            self.reports.append(rep)
+            self.latencies.append(time.perf_counter() - t0)
+            return rep
         self.reports.append(rep)
         self.it_in_step += 1
-        if rep["converged"] or self.it_in_step >= self.cap:
+        if rep["converged"]:
             new_alpha = self.g.hf_check_fracture_criterion()
-            if new_alpha == 0 or self.it_in_step >= 3 * self.cap:
+            self.rounds += 1
+            if new_alpha == 0 or self.rounds >= 4:
                 self.g.hf_accept_step()
+                self.accepted += 1
                 self.it_in_step = 0
+                self.rounds = 0
+                self.saved = self.g.hf_get_state()
+                if self.dt < self.dt0:
+                    self._set_dt(min(self.dt0, self.dt * 1.5))
+            else:
+                self.it_in_step = 0
+        elif self.it_in_step >= self.cap or not rep["lin_converged"]:
+            self._restart_step()
         self.latencies.append(time.perf_counter() - t0)
         return rep
 
@@ -180,7 +225,7 @@ def run_ours(args):
     g = make_problem(wl, prec, stream.cuda_stream, args.jacobi_block, args.restart)
     U, P, al, be = wl.seed()
     g.hf_set_state(U, P, al, be)
-    loop = NewtonLoop(g)
+    loop = NewtonLoop(g, wl)
     for _ in range(args.warmup):
         loop.step()
     stats = g.hf_get_stats()
@@ -221,7 +266,7 @@ def run_ours(args):
         g.hf_set_solver(precision="fp64", restart=args.restart, rtol=1e-8, max_iters=20000,
                         jacobi_block=args.jacobi_block, newton_tol=1e-8)
         g.hf_set_state(U, P, al, be)
-        l64 = NewtonLoop(g)
+        l64 = NewtonLoop(g, wl)
         for _ in range(min(args.warmup, 2)):
             l64.step()
         l64.reports.clear()

@@ -321,10 +321,29 @@ static hf_status build_subdomains(hf_mesh* h, int G) {
   for (int s = 0; s < nsd; ++s) h->levels_max = std::max(h->levels_max, sd_nlvl[s]);
   h->n_subdomain_slots = 0;
   h->n_interior_slots = 0;
+  std::vector<long long> rec_fwd(ne), rec_bwd(ne);
+  const long long bs = (long long)h->ned * h->nfr, dsz = (long long)h->ned * h->ned;
+  long long off = 0;
   for (int e = 0; e < ne; ++e) {
     h->n_subdomain_slots += __builtin_popcount((unsigned)(low[e] | up[e]));
     for (int j = 0; j < nsl; ++j) h->n_interior_slots += h->h_nbr[j * ne + e] >= 0;
   }
+  for (int s = 0; s < nsd; ++s) {
+    int b = s * G, c = std::min(G, ne - b);
+    for (int k = 0; k < c; ++k) {  // forward stream, level order
+      int e = sd_elems[b + k];
+      rec_fwd[e] = off;
+      off += __builtin_popcount((unsigned)low[e]) * bs;
+    }
+    for (int k = c - 1; k >= 0; --k) {  // backward stream, reverse level order
+      int e = sd_elems[b + k];
+      rec_bwd[e] = off;
+      off += __builtin_popcount((unsigned)up[e]) * bs + dsz;
+    }
+  }
+  h->d.rec_fwd = upload(h, rec_fwd);
+  h->d.rec_bwd = upload(h, rec_bwd);
+  if (!h->d.rec_fwd || !h->d.rec_bwd) return set_error(h, HF_ERR_OOM, "ILU record offsets");
   return check_cuda(h, cudaGetLastError(), "build_subdomains");
 }
 
@@ -633,6 +652,7 @@ hf_status hf_mesh_create(const hf_mesh_desc* desc, void* cuda_stream, hf_mesh** 
   d.ubar = upload(h, ubar);
   d.fext = dzeros<double>(h, h->nu);
   d.scal = dzeros<double>(h, 16);
+  d.err_flag = dzeros<int>(h, 4);
   h->fneu_trac = upload(h, ftrac);
   h->fneu = upload(h, fneu);
   size_t nmat = (size_t)ne * (h->ned * h->ned + nsl * h->ned * h->nfr);
@@ -650,7 +670,7 @@ hf_status hf_mesh_create(const hf_mesh_desc* desc, void* cuda_stream, hf_mesh** 
   if (!d.xyz || !d.enode || !d.grad_lam || !d.vol || !d.nbr || !d.slot_face || !d.slot_side || !d.dirmask ||
       !d.nlmask || !d.fe || !d.fl || !d.fnormal || !d.farea || !d.fh || !d.fsg || !d.loc_m || !d.loc_p ||
       !d.fpdof || !d.crack || !d.alpha || !d.beta || !d.w_old || !d.nl || !d.pinc_ptr || !d.pinc_face ||
-      !d.pinc_a || !d.p_active || !d.inj_w || !d.ubar || !d.fext || !d.scal || !h->fneu_trac || !h->fneu ||
+      !d.pinc_a || !d.p_active || !d.inj_w || !d.ubar || !d.fext || !d.scal || !d.err_flag || !h->fneu_trac || !h->fneu ||
       !h->J64.dg || !h->X || !h->R || !h->D || !h->tmp64 || !h->r64 || !h->d_elist || !h->d_count ||
       !h->d_red || !h->d_wtmp)
     return fail(HF_ERR_OOM, "device allocation failed");

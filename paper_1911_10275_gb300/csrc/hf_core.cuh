@@ -142,6 +142,9 @@ struct DevMesh {
   int* sd_lvl;              // level offsets into sd_elems, per subdomain
   int* sd_lvl_base;         // [nsd] index of the subdomain's first offset in sd_lvl
   int* sd_nlvl;             // [nsd]
+  long long* rec_fwd;       // [ne] start of the element's forward segment (L blocks)
+  long long* rec_bwd;       // [ne] start of the element's backward segment (U blocks, Dinv)
+  int* err_flag;            // [0]: a bounded wait in a kernel gave up
   // parameters
   double lam, mu, sigma_c, delta_c, b_stab;
   double mu_f, Q0, delta_f, dt, p_v;
@@ -227,6 +230,19 @@ __device__ __forceinline__ void face_to_elem_lam(const DevMesh& m, int f, int si
     lam[loc] = flam[v];
   }
 }
+
+// ILU factor layout: per subdomain, a forward stream (the L blocks of its
+// lower slots, element after element in level order) followed by a backward
+// stream (U blocks of the upper slots then Dinv, element after element in
+// reverse level order).  A warp solving the subdomain reads each stream front
+// to back.  Blocks hold ned columns x nfr face rows (rows fastest), slots in
+// ascending order; Dinv is ned x ned column-major.
+__host__ __device__ inline int slots_below(unsigned mask, int j) {
+  int c = 0;
+  for (int t = 0; t < j; ++t) c += (mask >> t) & 1u;
+  return c;
+}
+__host__ __device__ inline int nbits(unsigned mask) { return slots_below(mask, 8); }
 
 // traction-separation law with the contact penalty for w < 0 and zero
 // traction beyond delta_c

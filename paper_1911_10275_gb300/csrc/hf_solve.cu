@@ -128,6 +128,68 @@ template <int DIM> struct SpmvGroups {
   static constexpr int R = 2 * DIM;               // rows per group
 };
 
+// facet terms of cohesive (alpha) and fluid (beta) facets for the rows of
+// node group GRP only, added into that group's accumulators
+template <typename T, int DIM, int MODE, int GRP>
+__device__ void add_nl_rows(const DevMesh& m, int e, unsigned nlm, const T* __restrict__ x, T* acc) {
+  using S = Shape<DIM>;
+  using L = NL<DIM>;
+  constexpr int F = S::nfn, NED = S::ned, R = SpmvGroups<DIM>::R;
+  unsigned dmask = m.dirmask[e];
+  for (int j = 0; j < DIM + 1; ++j) {
+    bool al = (nlm >> j) & 1u, be = (nlm >> (4 + j)) & 1u;
+    if (!al && !be) continue;
+    int f = m.slot_face[j * m.ne + e];
+    int s = m.slot_side[j * m.ne + e];
+    // face nodes of this facet that belong to the group
+    bool any = false;
+    for (int a = 0; a < F; ++a) {
+      int loc = s == 0 ? m.loc_m[a * m.nf + f] : m.loc_p[a * m.nf + f];
+      any |= (loc / 2 == GRP);
+    }
+    if (!any) continue;
+    const double* rec = m.nl + (long long)f * S::nld;
+    double n[DIM];
+    for (int k = 0; k < DIM; ++k) n[k] = m.fnormal[k * m.nf + f];
+    double jn[F], xp[F];
+    if (MODE == 0) {
+      int em = m.fe[f], ep = m.fe[m.nf + f];
+      for (int b = 0; b < F; ++b) {
+        int lm = m.loc_m[b * m.nf + f], lp = m.loc_p[b * m.nf + f];
+        double sacc = 0.0;
+        for (int k = 0; k < DIM; ++k)
+          sacc += n[k] * ((double)x[(long long)ep * NED + lp * DIM + k] - (double)x[(long long)em * NED + lm * DIM + k]);
+        jn[b] = sacc;
+        int pd = m.fpdof[b * m.nf + f];
+        xp[b] = (be && pd >= 0) ? (double)x[m.nu + pd] : 0.0;
+      }
+    }
+    double sg = s == 0 ? -1.0 : 1.0;
+    for (int a = 0; a < F; ++a) {
+      int loc = s == 0 ? m.loc_m[a * m.nf + f] : m.loc_p[a * m.nf + f];
+      if (loc / 2 != GRP) continue;
+      double v = 0.0;
+      if (MODE == 0) {
+        for (int b = 0; b < F; ++b) {
+          if (al) v += rec[L::Tm + a * F + b] * jn[b];
+          if (be) v -= rec[L::Mm + a * F + b] * xp[b];
+        }
+      } else {
+        v = (al ? rec[L::rc + a] : 0.0) - (be ? rec[L::rp + a] : 0.0);
+      }
+      for (int k = 0; k < DIM; ++k) {
+        int row = loc * DIM + k;
+        if ((dmask >> row) & 1u) continue;
+        int rl = (loc % 2) * DIM + k;
+        T add = (T)(sg * n[k] * v);
+#pragma unroll
+        for (int q = 0; q < R; ++q)
+          if (q == rl) acc[q] += add;
+      }
+    }
+  }
+}
+
 template <typename T, int DIM, int MODE, int GRP>
 __device__ __forceinline__ void spmv_group(const DevMesh& m, const T* __restrict__ dg, const T* __restrict__ off,
                                            const T* __restrict__ x, T* __restrict__ y, int e) {
@@ -166,6 +228,8 @@ __device__ __forceinline__ void spmv_group(const DevMesh& m, const T* __restrict
       }
     }
   }
+  unsigned nlm = m.nlmask[e];
+  if (nlm) add_nl_rows<T, DIM, MODE, GRP>(m, e, nlm, x, acc);
   T* ye = y + (long long)e * NED + R0;
   if (MODE == 1) {
     unsigned dm = m.dirmask[e];
@@ -198,12 +262,6 @@ __global__ void __launch_bounds__(32 * SpmvGroups<DIM>::P) k_spmv(DevMesh m, con
       case 3: if (DIM == 3) spmv_group<T, DIM, MODE, 3>(m, dg, off, x, y, e); break;
       case 4: if (DIM == 3) spmv_group<T, DIM, MODE, 4>(m, dg, off, x, y, e); break;
     }
-  }
-  // facet terms of cohesive and fluid facets touch rows of every group
-  __syncthreads();
-  if (warp == 0 && live) {
-    unsigned nlm = m.nlmask[e];
-    if (nlm) add_nl_terms<T, DIM, MODE>(m, e, nlm, x, y);
   }
 }
 
@@ -313,8 +371,11 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
     int lo = m.sd_lvl[lb + lv], hi = m.sd_lvl[lb + lv + 1];
     for (int idx = lo + warp; idx < hi; idx += nw) {
       int i = m.sd_elems[idx];
-      T* rec = lu + (long long)i * LUS;
+      T* recf = lu + m.rec_fwd[i];
+      T* recb = lu + m.rec_bwd[i];
       unsigned nlm = m.nlmask[i];
+      const unsigned low_i = m.lowmask[i], up_i = m.upmask[i];
+      const int nlow_i = nbits(low_i), nup_i = nbits(up_i);
       for (int t = lane; t < NED * NED; t += 32) {
         int r = t / NED, c = t % NED;
         Am[r * NED + c] = (T)dg[((long long)c * NED + r) * ne + i];
@@ -324,9 +385,8 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
         if ((nlm >> j) & 1u) cohesive_patch_rows<T, DIM>(m, i, j, 0, Am, NED, true, lane);
         __syncwarp();
       }
-      unsigned low = m.lowmask[i], up = m.upmask[i];
       for (int j = 0; j < DIM + 1; ++j) {
-        if (!((low >> j) & 1u)) continue;
+        if (!((low_i >> j) & 1u)) continue;
         int k = m.nbr[j * ne + i];
         // A_ik (compact) into Lm
         for (int t = lane; t < NFR * NED; t += 32) {
@@ -337,7 +397,9 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
         if ((nlm >> j) & 1u) cohesive_patch_rows<T, DIM>(m, i, j, 1, Lm, NED, false, lane);
         __syncwarp();
         // L_ik = A_ik Dinv_k
-        const T* dk = lu + (long long)k * LUS;
+        const unsigned low_k = m.lowmask[k], up_k = m.upmask[k];
+        const T* reckb = lu + m.rec_bwd[k];
+        const T* dk = reckb + nbits(up_k) * NED * NFR;
         T lrow[NED];
         if (lane < NFR) {
 #pragma unroll
@@ -353,7 +415,7 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
 #pragma unroll
           for (int c = 0; c < NED; ++c) {
             Lm[lane * NED + c] = lrow[c];
-            rec[NED * NED + j * NED * NFR + c * NFR + lane] = lrow[c];
+            recf[slots_below(low_i, j) * NED * NFR + c * NFR + lane] = lrow[c];
           }
         }
         __syncwarp();
@@ -361,7 +423,7 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
         int jk = 0;
         for (int t = 0; t < DIM + 1; ++t)
           if (m.nbr[t * ne + k] == i) jk = t;
-        const T* uk = lu + (long long)k * LUS + NED * NED + jk * NED * NFR;
+        const T* uk = reckb + slots_below(up_k, jk) * NED * NFR;
         for (int t = lane; t < NFR * NED; t += 32) {
           int rr = t / NED, c = t % NED;
           T sacc = (T)0;
@@ -375,7 +437,7 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
         __syncwarp();
       }
       for (int j = 0; j < DIM + 1; ++j) {
-        if (!((up >> j) & 1u)) continue;
+        if (!((up_i >> j) & 1u)) continue;
         for (int t = lane; t < NFR * NED; t += 32) {
           int rr = t / NED, c = t % NED;
           Lm[rr * NED + c] = (T)off[(((long long)j * NED + c) * NFR + rr) * ne + i];
@@ -385,14 +447,15 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
         __syncwarp();
         for (int t = lane; t < NFR * NED; t += 32) {
           int rr = t / NED, c = t % NED;
-          rec[NED * NED + j * NED * NFR + c * NFR + rr] = Lm[rr * NED + c];
+          recb[slots_below(up_i, j) * NED * NFR + c * NFR + rr] = Lm[rr * NED + c];
         }
         __syncwarp();
       }
       warp_invert<T, DIM>(Am, lane);
+      T* dinv = recb + nup_i * NED * NFR;
       for (int t = lane; t < NED * NED; t += 32) {
         int c = t / NED, r = t % NED;
-        rec[c * NED + r] = Am[r * NED + c];
+        dinv[c * NED + r] = Am[r * NED + c];
       }
       __syncwarp();
     }
@@ -423,7 +486,7 @@ __global__ void k_schur(DevMesh m, const T* __restrict__ lu, T* sinv) {
     double v = rec[L::Dm + ga * F + ga];
     for (int s = 0; s < 2; ++s) {
       int e = m.fe[s * m.nf + f];
-      const T* di = lu + (long long)e * LUS;
+      const T* di = lu + m.rec_bwd[e] + nbits(m.upmask[e]) * NED * S::nfr;
       for (int b = 0; b < F; ++b) {
         int lb = s == 0 ? m.loc_m[b * m.nf + f] : m.loc_p[b * m.nf + f];
         double cs = rec[L::Cs + ga * F + b];
@@ -444,88 +507,191 @@ __global__ void k_schur(DevMesh m, const T* __restrict__ lu, T* sinv) {
   sinv[g] = (T)(1.0 / Sg);
 }
 
-// z = M^-1 (scale * rin); optionally writes v = scale * rin.  One CTA per subdomain.
-template <typename T, int DIM>
-__global__ void __launch_bounds__(128) k_ilu_apply(DevMesh m, const T* __restrict__ lu, const T* __restrict__ rin,
-                                                   const double* scale, T* vout, T* z, const int* skip) {
+// ---- TMA bulk copies and mbarriers (shared-memory staging of ILU records)
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+  return (unsigned)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* bar) {
+  // order earlier generic-proxy reads of dst before the async-proxy write
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+// bounded wait on an mbarrier phase; on timeout raise the error flag and go on
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned phase, int* err) {
+  for (int it = 0; it < (1 << 22); ++it) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(phase)
+        : "memory");
+    if (ok) return;
+  }
+  atomicExch(err, 1);
+}
+
+// z = M^-1 rin on the displacement unknowns.  One warp per subdomain, no
+// block-level barriers: the warp solves its subdomain's forward sweep then
+// its backward sweep element after element in (reverse) level order.  Its
+// factor streams are read front to back through a per-warp ring in shared
+// memory, filled by TMA bulk copies up to APPLY_NQ segments ahead of the
+// element being solved, so HBM latency is hidden behind the solve.
+constexpr int APPLY_NQ = 8;
+
+template <typename T, int DIM> struct ApplyRing {
+  static constexpr int BS = Shape<DIM>::ned * Shape<DIM>::nfr;
+  static constexpr int SEG = (DIM + 1) * BS + Shape<DIM>::ned * Shape<DIM>::ned;  // largest segment
+  static constexpr int RINGV = SEG + 4 * BS;                                       // ring capacity (values)
+};
+
+template <typename T, int DIM, int W>
+__global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __restrict__ lu, const T* __restrict__ rin,
+                                                      T* z, const int* skip) {
   using S = Shape<DIM>;
-  constexpr int NED = S::ned, NFR = S::nfr, LUS = S::lus;
+  using RGN = ApplyRing<T, DIM>;
+  constexpr int NED = S::ned, NFR = S::nfr, BS = RGN::BS, RINGV = RGN::RINGV, NQ = APPLY_NQ;
   if (skip && *skip) return;
-  extern __shared__ __align__(16) unsigned char smraw[];
-  int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  int s = blockIdx.x;
-  int base = s * m.G;
-  int cnt = min(m.G, m.ne - base);
-  T* ys = reinterpret_cast<T*>(smraw);
-  T* tmp = ys + m.G * NED + warp * 32;
-  T sc = scale ? (T)(*scale) : (T)1;
-  for (int t = threadIdx.x; t < cnt * NED; t += blockDim.x) {
-    T v = rin[(long long)base * NED + t] * sc;
-    ys[t] = v;
-    if (vout) vout[(long long)base * NED + t] = v;
-  }
+  extern __shared__ __align__(128) unsigned char smraw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // per-warp region: ring | ys | tmp | queue starts | barriers
+  const size_t per_warp =
+      ((size_t)(RINGV + m.G * NED + 32) * sizeof(T) + NQ * sizeof(long long) + NQ * 8 + 127) / 128 * 128;
+  unsigned char* region = smraw + (size_t)warp * per_warp;
+  T* ring = reinterpret_cast<T*>(region);
+  T* ys = ring + RINGV;
+  T* tmp = ys + (size_t)m.G * NED;
+  long long* qstart = reinterpret_cast<long long*>(tmp + 32);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(qstart + NQ);
+  if (lane < NQ) mbar_init(&bars[lane], 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
-  int lb = m.sd_lvl_base[s], nl = m.sd_nlvl[s];
+  const int s = blockIdx.x * W + warp;
+  if (s >= m.nsd) return;
+  const int base = s * m.G, cnt = min(m.G, m.ne - base);
   const long long ne = m.ne;
-  // forward: y_i = r_i - sum_{k lower} L_ik y_k
-  for (int lv = 0; lv < nl; ++lv) {
-    int lo = m.sd_lvl[lb + lv], hi = m.sd_lvl[lb + lv + 1];
-    for (int idx = lo + warp; idx < hi; idx += nw) {
-      int i = m.sd_elems[idx];
+  for (int t = lane; t < cnt * NED; t += 32) ys[t] = rin[(long long)base * NED + t];
+  __syncwarp();
+  const int* order = m.sd_elems + base;  // level order
+  // ring state (identical in every lane; lane 0 issues the copies)
+  long long vhead = 0, vtail = 0;
+  unsigned qh = 0, qt = 0;
+  int issue_k = 0;
+
+  for (int sweep = 0; sweep < 2; ++sweep) {
+    issue_k = 0;
+    auto elem = [&](int k) { return sweep == 0 ? order[k] : order[cnt - 1 - k]; };
+    auto seg_size = [&](int e) -> int {
+      return sweep == 0 ? nbits(m.lowmask[e]) * BS : nbits(m.upmask[e]) * BS + NED * NED;
+    };
+    auto seg_src = [&](int e) -> const T* { return lu + (sweep == 0 ? m.rec_fwd[e] : m.rec_bwd[e]); };
+    auto produce = [&]() {
+      while (issue_k < cnt && qh - qt < (unsigned)NQ) {
+        int e = elem(issue_k);
+        int sz = seg_size(e);
+        if (sz == 0) {
+          ++issue_k;
+          continue;
+        }
+        if (qh == qt) {  // nothing in flight: restart at the ring origin
+          vhead = (vhead + RINGV - 1) / RINGV * RINGV;
+          vtail = vhead;
+        }
+        long long pos = vhead % RINGV;
+        long long pad = (pos + sz > RINGV) ? RINGV - pos : 0;
+        if (vhead + pad + sz - vtail > RINGV) break;  // wait for the consumer to free space
+        vhead += pad;
+        long long start = vhead;
+        vhead += sz;
+        if (lane == 0) {
+          qstart[qh % NQ] = start;
+          bulk_load(ring + start % RINGV, seg_src(e), (unsigned)(sz * sizeof(T)), &bars[qh % NQ]);
+        }
+        ++qh;
+        ++issue_k;
+      }
+      __syncwarp();
+    };
+    produce();
+    for (int k = 0; k < cnt; ++k) {
+      int i = elem(k);
       int li = i - base;
-      unsigned low = m.lowmask[i];
-      const T* rec = lu + (long long)i * LUS;
-      for (int j = 0; j < DIM + 1; ++j) {
-        if (!((low >> j) & 1u)) continue;
-        int lk = m.nbr[j * ne + i] - base;
-        const T* blk = rec + NED * NED + j * NED * NFR;
-        T dot = (T)0;
-        if (lane < NFR) {
+      int sz = seg_size(i);
+      const T* blk = nullptr;
+      if (sz) {
+        unsigned q = qt % NQ;
+        mbar_wait(&bars[q], (qt / NQ) & 1u, m.err_flag);
+        blk = ring + qstart[q] % RINGV;
+      }
+      if (sweep == 0) {
+        // y_i = r_i - sum_{lower k} L_ik y_k
+        unsigned low = m.lowmask[i];
+        int qb = 0;
+        for (int j = 0; j < DIM + 1; ++j) {
+          if (!((low >> j) & 1u)) continue;
+          int lk = m.nbr[j * ne + i] - base;
+          T d0 = (T)0, d1 = (T)0;
+          if (lane < NFR) {
 #pragma unroll
-          for (int c = 0; c < NED; ++c) dot += blk[c * NFR + lane] * ys[lk * NED + c];
+            for (int c = 0; c < NED; c += 2) {
+              d0 += blk[qb * BS + c * NFR + lane] * ys[lk * NED + c];
+              d1 += blk[qb * BS + (c + 1) * NFR + lane] * ys[lk * NED + c + 1];
+            }
+          }
+          __syncwarp();
+          if (lane < NFR) ys[li * NED + face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= d0 + d1;
+          __syncwarp();
+          ++qb;
+        }
+      } else {
+        // z_i = Dinv_i (y_i - sum_{upper j} U_ij z_j)
+        unsigned up = m.upmask[i];
+        if (lane < NED) tmp[lane] = ys[li * NED + lane];
+        __syncwarp();
+        int qb = 0;
+        for (int j = 0; j < DIM + 1; ++j) {
+          if (!((up >> j) & 1u)) continue;
+          int lk = m.nbr[j * ne + i] - base;
+          T d0 = (T)0, d1 = (T)0;
+          if (lane < NFR) {
+#pragma unroll
+            for (int c = 0; c < NED; c += 2) {
+              d0 += blk[qb * BS + c * NFR + lane] * ys[lk * NED + c];
+              d1 += blk[qb * BS + (c + 1) * NFR + lane] * ys[lk * NED + c + 1];
+            }
+          }
+          __syncwarp();
+          if (lane < NFR) tmp[face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= d0 + d1;
+          __syncwarp();
+          ++qb;
+        }
+        const T* dinv = blk + qb * BS;
+        T z0 = (T)0, z1 = (T)0;
+        if (lane < NED) {
+#pragma unroll
+          for (int c = 0; c < NED; c += 2) {
+            z0 += dinv[c * NED + lane] * tmp[c];
+            z1 += dinv[(c + 1) * NED + lane] * tmp[c + 1];
+          }
         }
         __syncwarp();
-        if (lane < NFR) ys[li * NED + face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= dot;
+        if (lane < NED) ys[li * NED + lane] = z0 + z1;
         __syncwarp();
       }
+      if (sz) {
+        ++qt;
+        vtail = (qt < qh) ? qstart[qt % NQ] : vhead;
+      }
+      produce();
     }
-    __syncthreads();
   }
-  // backward: z_i = Dinv_i (y_i - sum_{j upper} U_ij z_j)
-  for (int lv = nl - 1; lv >= 0; --lv) {
-    int lo = m.sd_lvl[lb + lv], hi = m.sd_lvl[lb + lv + 1];
-    for (int idx = lo + warp; idx < hi; idx += nw) {
-      int i = m.sd_elems[idx];
-      int li = i - base;
-      unsigned up = m.upmask[i];
-      const T* rec = lu + (long long)i * LUS;
-      if (lane < NED) tmp[lane] = ys[li * NED + lane];
-      __syncwarp();
-      for (int j = 0; j < DIM + 1; ++j) {
-        if (!((up >> j) & 1u)) continue;
-        int lk = m.nbr[j * ne + i] - base;
-        const T* blk = rec + NED * NED + j * NED * NFR;
-        T dot = (T)0;
-        if (lane < NFR) {
-#pragma unroll
-          for (int c = 0; c < NED; ++c) dot += blk[c * NFR + lane] * ys[lk * NED + c];
-        }
-        __syncwarp();
-        if (lane < NFR) tmp[face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= dot;
-        __syncwarp();
-      }
-      T zr = (T)0;
-      if (lane < NED) {
-#pragma unroll
-        for (int c = 0; c < NED; ++c) zr += rec[c * NED + lane] * tmp[c];
-      }
-      __syncwarp();
-      if (lane < NED) ys[li * NED + lane] = zr;
-      __syncwarp();
-    }
-    __syncthreads();
-  }
-  for (int t = threadIdx.x; t < cnt * NED; t += blockDim.x) z[(long long)base * NED + t] = ys[t];
+  for (int t = lane; t < cnt * NED; t += 32) z[(long long)base * NED + t] = ys[t];
 }
 
 // pressure part of the preconditioner (after the displacement part)
@@ -633,13 +799,24 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
     for (int c = 0; c < 32; ++c)
       if (c < ncols) acc[c] += V[c * ldv + i] * wv;
   }
+  // block reduction by transposition: warp w writes its 32 accumulators as
+  // row lane of a 32x32 tile; lane c then adds column c (working precision,
+  // 32 adds) and the 8 warp results meet in double
+  constexpr int CH = sizeof(T) == 4 ? 32 : 16;   // columns per pass (static smem < 48 KB)
+  __shared__ T tile[RB / 32][32][CH + 1];
   int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
-  for (int c = 0; c < 32; ++c) {
-    if (c < ncols) {
-      double v = warp_sum((double)acc[c]);
-      if (lane == 0) sm[warp][c] = v;
+  for (int c0 = 0; c0 < 32; c0 += CH) {
+#pragma unroll
+    for (int c = 0; c < CH; ++c) tile[warp][lane][c] = acc[c0 + c];
+    __syncwarp();
+    if (lane < CH) {
+      T colsum = (T)0;
+#pragma unroll
+      for (int l = 0; l < 32; ++l) colsum += tile[warp][l][lane];
+      sm[warp][c0 + lane] = (double)colsum;
     }
+    __syncwarp();
   }
   __syncthreads();
   if (threadIdx.x < ncols) {
@@ -652,9 +829,18 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
   __syncthreads();
   if (last) {
-    for (int c = 0; c < ncols; ++c) {
-      double s = block_sum_partials(partial, gridDim.x, 32, c);
-      if (threadIdx.x == 0) gs->H[j * 31 + c] = s;
+    // one pass over all columns: thread (grp, c) sums rows b = grp, grp+8, ...
+    // of the partial table, then column c adds the 8 groups in order
+    __shared__ double red[RB / 32][32];
+    int c = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    double sacc = 0.0;
+    for (int b = grp; b < (int)gridDim.x; b += RB / 32) sacc += __ldcg(partial + (long long)b * 32 + c);
+    red[grp][c] = sacc;
+    __syncthreads();
+    if (threadIdx.x < ncols) {
+      double tot = 0.0;
+      for (int g2 = 0; g2 < RB / 32; ++g2) tot += red[g2][threadIdx.x];
+      gs->H[j * 31 + threadIdx.x] = tot;
     }
     if (threadIdx.x == 0) *counter = 0;
   }
@@ -669,7 +855,7 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
   int ncols = j + 1;
   if (threadIdx.x < 32) h[threadIdx.x] = threadIdx.x < ncols ? (T)gs->H[j * 31 + threadIdx.x] : (T)0;
   __syncthreads();
-  double acc = 0.0;
+  T acc_t = (T)0;
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
     T ww = w[i];
@@ -677,9 +863,9 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
     for (int c = 0; c < 32; ++c)
       if (c < ncols) ww -= h[c] * V[c * ldv + i];
     w[i] = ww;
-    acc += (double)ww * (double)ww;
+    acc_t += ww * ww;
   }
-  if (!block_partial_last(acc, partial, counter)) return;
+  if (!block_partial_last((double)acc_t, partial, counter)) return;
   double nrm2 = block_sum_partials(partial, gridDim.x, 1, 0);
   if (threadIdx.x == 0) {
     double nrm = sqrt(nrm2);
@@ -1001,15 +1187,36 @@ static void spmv(hf_mesh* h, const T* dg, const T* off, const T* x, T* y, const 
   { note_launch(); k_spmv<T, DIM, MODE><<<eb + pb, nt, 0, h->stream>>>(h->d, dg, off, x, y, eb, skip); }
 }
 
+template <int DIM, typename T> static size_t apply_smem(int G, int W) {
+  using S = Shape<DIM>;
+  size_t per_warp =
+      ((size_t)(ApplyRing<T, DIM>::RINGV + G * S::ned + 32) * sizeof(T) + APPLY_NQ * 8 + APPLY_NQ * 8 + 127) / 128 * 128;
+  return (size_t)W * per_warp;
+}
+
+template <typename T, int DIM, int W>
+static void launch_apply(hf_mesh* h, const T* lu, const T* rin, T* z, const int* skip) {
+  size_t sm = apply_smem<DIM, T>(h->G, W);
+  static size_t configured = 0;
+  if (sm > 48 * 1024 && sm > configured) {
+    cudaFuncSetAttribute(k_ilu_apply<T, DIM, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    configured = sm;
+  }
+  { note_launch(); k_ilu_apply<T, DIM, W><<<(h->d.nsd + W - 1) / W, 32 * W, sm, h->stream>>>(h->d, lu, rin, z, skip); }
+}
+
 template <typename T, int DIM>
 static void precond(hf_mesh* h, const Krylov<T>& K, const T* rin, const double* scale, T* vout, T* z,
                     const int* skip) {
-  using S = Shape<DIM>;
-  size_t sm = ((size_t)h->G * S::ned + 4 * 32) * sizeof(T);
-  if (sm > 48 * 1024) cudaFuncSetAttribute(k_ilu_apply<T, DIM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  { note_launch(); k_ilu_apply<T, DIM><<<h->d.nsd, 128, sm, h->stream>>>(h->d, K.lu, rin, scale, vout, z, skip); }
+  (void)scale;
+  (void)vout;
+  // warps (subdomains) per CTA: as many as keep at least two CTAs per SM busy
+  int nsd = h->d.nsd;
+  if (nsd >= 4 * 2 * 152) launch_apply<T, DIM, 4>(h, K.lu, rin, z, skip);
+  else if (nsd >= 2 * 2 * 152) launch_apply<T, DIM, 2>(h, K.lu, rin, z, skip);
+  else launch_apply<T, DIM, 1>(h, K.lu, rin, z, skip);
   if (h->np > 0)
-    { note_launch(); k_prec_p<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, rin, scale, vout, K.sinv, z, skip); }
+    { note_launch(); k_prec_p<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, rin, nullptr, nullptr, K.sinv, z, skip); }
 }
 
 // one GMRES(m) cycle on x (V[0] and gs already set by k_residual_start)
@@ -1169,6 +1376,14 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
     rep->refinements = refinements;
     rep->lin_res = rnorm / bnorm;
     rep->lin_converged = rnorm <= tol;
+  }
+  // a bounded wait inside a kernel that gave up leaves its flag behind
+  int flag = 0;
+  cudaMemcpyAsync(&flag, h->d.err_flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+  cudaStreamSynchronize(h->stream);
+  if (flag) {
+    cudaMemsetAsync(h->d.err_flag, 0, sizeof(int), h->stream);
+    return set_error(h, HF_ERR_TIMEOUT, "a bounded device wait timed out in the preconditioner");
   }
   return st;
 }
