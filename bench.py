@@ -223,6 +223,9 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     prec = "mixed" if args.precision == "mixed" else "fp64"
     g = make_problem(wl, prec, stream.cuda_stream, args.jacobi_block, args.restart)
+    if args.graphs:
+        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
+                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=1)
     U, P, al, be = wl.seed()
     g.hf_set_state(U, P, al, be)
     loop = NewtonLoop(g, wl)
@@ -250,6 +253,22 @@ def run_ours(args):
     ms = ev0.elapsed_time(ev1)
     ktimes = g.hf_get_kernel_times()
     g.hf_set_profiling(False)
+    timing_source = "CUDA events on the library stream inside the timed region"
+    if args.graphs and ktimes["spmv"][1] == 0:
+        # this driver/toolkit gave no timing for events recorded inside graphs:
+        # time the kernels with events on the same state, graphs off, right after
+        code = g.hf_get_stats()["graph_timing_error"]
+        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
+                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=0)
+        g.hf_set_profiling(True)
+        for _ in range(2):
+            loop.step()
+        ktimes = g.hf_get_kernel_times()
+        g.hf_set_profiling(False)
+        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
+                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=args.graphs)
+        timing_source = ("CUDA events over 2 Newton iterations right after the timed region, same state, "
+                         f"graphs off (graph-node event timing unavailable: CUDA error {code})")
     stats = g.hf_get_stats()
     launches = stats["kernel_launches"] - launches0
     reports = list(loop.reports)
@@ -260,11 +279,34 @@ def run_ours(args):
         ms = float(t.item())
     value = args.steps * world / (ms / 1000.0)
 
+    # end to end through the public API with host buffers: the same time
+    # loop, but every step uploads the state from pinned host memory and reads
+    # the updated state back
+    e2e = None
+    if args.e2e_steps > 0:
+        le = loop  # continue the timed time loop from where it stopped
+        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        host = [pin(x) for x in g.hf_get_state()[:5]] + [0.0]
+        h2d = sum(x.nbytes for x in host[:5])
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            g.hf_set_state(*host[:5], host[5])
+            le.step()
+            out = g.hf_get_state()
+            for dst, src in zip(host[:5], out[:5]):
+                dst[...] = src
+            host[5] = out[5]
+        torch.cuda.synchronize(dev)
+        te = time.perf_counter() - t0
+        e2e = {"value": args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(h2d), "steps": args.e2e_steps}
+
     # FP64 beside it on the same starting state (fewer steps)
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0:
-        g.hf_set_solver(precision="fp64", restart=args.restart, rtol=1e-8, max_iters=20000,
-                        jacobi_block=args.jacobi_block, newton_tol=1e-8)
+        g.hf_set_solver(precision="fp64", restart=args.restart, rtol=1e-8, max_iters=3000,
+                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=args.graphs)
         g.hf_set_state(U, P, al, be)
         l64 = NewtonLoop(g, wl)
         for _ in range(min(args.warmup, 2)):
@@ -281,31 +323,8 @@ def run_ours(args):
         fp64 = {"value": args.fp64_steps / (ms64 / 1000.0), "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
                 "gmres_iters_per_newton": float(np.mean([r["gmres_iters"] for r in l64.reports]))}
-        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=20000,
-                        jacobi_block=args.jacobi_block, newton_tol=1e-8)
-
-    # end to end through the public API with host buffers
-    e2e = None
-    if args.e2e_steps > 0:
-        g.hf_set_state(U, P, al, be)
-        Uh, Ph, ah, bh, wh, th = g.hf_get_state()
-        pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
-        Uh, Ph, ah, bh, wh = pin(Uh), pin(Ph), pin(ah), pin(bh), pin(wh)
-        h2d = Uh.nbytes + Ph.nbytes + ah.nbytes + bh.nbytes + wh.nbytes
-        d2h = 0
-        torch.cuda.synchronize(dev)
-        t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            g.hf_set_state(Uh, Ph, ah, bh, wh, th)
-            g.hf_newton_step()
-            out = g.hf_get_state()
-            Uh[:], Ph[:] = out[0], out[1]
-            wh[:] = out[4]
-            d2h = sum(x.nbytes for x in out[:5])
-        torch.cuda.synchronize(dev)
-        te = time.perf_counter() - t0
-        e2e = {"value": args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h)}
+        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
+                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=args.graphs)
 
     # roofline of the dominant kernel class, from the events of the timed region
     elt = 4 if prec == "mixed" else 8
@@ -333,7 +352,8 @@ def run_ours(args):
         "data": "synthetic (seeded structured P2 mesh and seed crack)",
         "config": {"workload": wl.name, "dofs": int(g.N), "elements": int(wl.mesh.n_elems),
                    "precision": prec, "gmres_rtol": 1e-8, "restart": args.restart,
-                   "jacobi_block": args.jacobi_block, "parallelism": f"replicas x{world}",
+                   "jacobi_block": args.jacobi_block, "cuda_graphs": bool(args.graphs),
+                   "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2 (matrix + factor %.2f GB per replica)" %
                          (2 * algo["spmv"] / 1e9)},
         "fp64": fp64,
@@ -341,6 +361,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "roofline": roofline,
         "kernel_ms": breakdown,
+        "kernel_timing_source": timing_source,
         "kernel_ms_total_share_of_step": total_ms / ms if ms else None,
         "gmres_iters_per_newton": float(np.mean(gmres)) if gmres else None,
         "newton_latency_ms": {"p50": 1000 * lat[len(lat) // 2], "p99": 1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
@@ -421,8 +442,9 @@ def main():
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--jacobi-block", dest="jacobi_block", type=int, default=32)
     ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--graphs", type=int, default=1)
     ap.add_argument("--fp64-steps", dest="fp64_steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=2)
+    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=4)
     ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     args = ap.parse_args()

@@ -201,7 +201,9 @@ hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
  * with a neighbour), [2] slots inside block-Jacobi subdomains, [3] deepest
  * level schedule, [4] subdomains, [5] nonlinear facets, [6] pressure
  * unknowns, [7] facets, [8] kernel launches issued by the library in this
- * process so far, [9..15] zero.  st holds 16. */
+ * process so far, [9] CUDA error met when reading timing events recorded
+ * inside a captured GMRES cycle (0: none; graph cycles then go untimed),
+ * [10..15] zero.  st holds 16. */
 hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
 
 const char* hf_last_error(const hf_mesh* h);

@@ -268,7 +268,7 @@ class HFMesh:
         st = np.zeros(16, np.int64)
         self._check(self.lib.hf_get_stats(self.h, _ptr(st, C.c_int64)))
         keys = ["elements", "interior_slots", "subdomain_slots", "levels_max", "subdomains", "nl_faces",
-                "n_p", "faces", "kernel_launches"]
+                "n_p", "faces", "kernel_launches", "graph_timing_error"]
         return dict(zip(keys, (int(x) for x in st)))
 
     def hf_solve_linear(self, rhs):

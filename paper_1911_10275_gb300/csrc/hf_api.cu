@@ -351,6 +351,13 @@ static void invalidate_graphs(hf_mesh* h) {
   if (h->graph64) cudaGraphExecDestroy(h->graph64);
   if (h->graph32) cudaGraphExecDestroy(h->graph32);
   h->graph64 = h->graph32 = nullptr;
+  for (auto* v : {&h->gev64, &h->gev32}) {
+    for (GraphEv& g : *v) {
+      cudaEventDestroy(g.a);
+      cudaEventDestroy(g.b);
+    }
+    v->clear();
+  }
 }
 
 static std::vector<int> all_subdomains(hf_mesh* h) {
@@ -1032,7 +1039,8 @@ hf_status hf_get_stats(const hf_mesh* h, int64_t* st) {
   st[6] = h->np;
   st[7] = h->nf;
   st[8] = launch_counter();
-  for (int i = 9; i < 16; ++i) st[i] = 0;
+  st[9] = h->prof.graph_timing_error;
+  for (int i = 10; i < 16; ++i) st[i] = 0;
   return HF_OK;
 }
 

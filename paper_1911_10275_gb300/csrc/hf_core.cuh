@@ -238,11 +238,19 @@ __device__ __forceinline__ void face_to_elem_lam(const DevMesh& m, int f, int si
 // to back.  Blocks hold ned columns x nfr face rows (rows fastest), slots in
 // ascending order; Dinv is ned x ned column-major.
 __host__ __device__ inline int slots_below(unsigned mask, int j) {
-  int c = 0;
-  for (int t = 0; t < j; ++t) c += (mask >> t) & 1u;
-  return c;
+#ifdef __CUDA_ARCH__
+  return __popc(mask & ((1u << j) - 1u));
+#else
+  return __builtin_popcount(mask & ((1u << j) - 1u));
+#endif
 }
-__host__ __device__ inline int nbits(unsigned mask) { return slots_below(mask, 8); }
+__host__ __device__ inline int nbits(unsigned mask) {
+#ifdef __CUDA_ARCH__
+  return __popc(mask);
+#else
+  return __builtin_popcount(mask);
+#endif
+}
 
 // traction-separation law with the contact penalty for w < 0 and zero
 // traction beyond delta_c

@@ -66,8 +66,20 @@ struct GmresState {
 enum ProfKind { PK_SPMV = 0, PK_PREC = 1, PK_ORTH = 2, PK_FACTOR = 3, PK_ASSEMBLY = 4, PK_SPMV64 = 5,
                 PK_UPDATE = 6, PK_COUNT = 8 };
 constexpr int PROF_EVENTS = 256;
+// event pair recorded as graph nodes inside a captured GMRES cycle; j is the
+// Arnoldi step it belongs to (-1: once per cycle)
+struct GraphEv {
+  int kind;
+  int j;
+  cudaEvent_t a, b;
+};
+
 struct Prof {
   bool on = false;
+  bool capturing = false;       // events go to the graph being captured
+  int cap_j = -1;
+  std::vector<GraphEv>* cap_list = nullptr;
+  int graph_timing_error = 0;   // CUDA error met reading graph-node events (0: none)
   cudaEvent_t ev[2 * PROF_EVENTS] = {};
   int kind[PROF_EVENTS] = {};
   int n = 0;
@@ -135,6 +147,7 @@ struct hf_mesh {
 
   // CUDA graphs of one GMRES cycle per precision
   cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
+  std::vector<hfk::GraphEv> gev64, gev32;  // timing events baked into the graphs
   hfk::Prof prof;
   long long n_interior_slots = 0, n_subdomain_slots = 0;
 };

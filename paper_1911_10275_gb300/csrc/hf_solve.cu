@@ -30,6 +30,31 @@ constexpr int RB = 256;  // threads of reduction kernels
 
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
+// 16-byte vectors for the Krylov kernels: 4 floats or 2 doubles per load
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  using type = float4;
+  static constexpr int n = 4;
+  __device__ static float dot(const float4& a, const float4& b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+  __device__ static void axpy(float4& y, float a, const float4& x) {
+    y.x -= a * x.x; y.y -= a * x.y; y.z -= a * x.z; y.w -= a * x.w;
+  }
+  __device__ static void fma(float4& y, float a, const float4& x) {
+    y.x += a * x.x; y.y += a * x.y; y.z += a * x.z; y.w += a * x.w;
+  }
+  __device__ static float4 scale(const float4& x, float a) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
+  __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+};
+template <> struct Vec<double> {
+  using type = double2;
+  static constexpr int n = 2;
+  __device__ static double dot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+  __device__ static void axpy(double2& y, double a, const double2& x) { y.x -= a * x.x; y.y -= a * x.y; }
+  __device__ static void fma(double2& y, double a, const double2& x) { y.x += a * x.x; y.y += a * x.y; }
+  __device__ static double2 scale(const double2& x, double a) { return make_double2(a * x.x, a * x.y); }
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+};
+
 // ------------------------------------------------------------------ SpMV
 // MODE 0: y = J x.  MODE 1 (T = double): y = R(x), the residual.
 template <typename T, int DIM, int MODE>
@@ -242,7 +267,7 @@ __device__ __forceinline__ void spmv_group(const DevMesh& m, const T* __restrict
 }
 
 template <typename T, int DIM, int MODE>
-__global__ void __launch_bounds__(32 * SpmvGroups<DIM>::P) k_spmv(DevMesh m, const T* __restrict__ dg,
+__global__ void __launch_bounds__(32 * SpmvGroups<DIM>::P, 5) k_spmv(DevMesh m, const T* __restrict__ dg,
                                                                    const T* __restrict__ off, const T* __restrict__ x,
                                                                    T* __restrict__ y, int eblocks, const int* skip) {
   if (skip && *skip) return;
@@ -548,7 +573,7 @@ constexpr int APPLY_NQ = 8;
 template <typename T, int DIM> struct ApplyRing {
   static constexpr int BS = Shape<DIM>::ned * Shape<DIM>::nfr;
   static constexpr int SEG = (DIM + 1) * BS + Shape<DIM>::ned * Shape<DIM>::ned;  // largest segment
-  static constexpr int RINGV = SEG + 4 * BS;                                       // ring capacity (values)
+  static constexpr int RINGV = SEG + BS;                                           // ring capacity (values)
 };
 
 template <typename T, int DIM, int W>
@@ -579,9 +604,9 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
   for (int t = lane; t < cnt * NED; t += 32) ys[t] = rin[(long long)base * NED + t];
   __syncwarp();
   const int* order = m.sd_elems + base;  // level order
-  // ring state (identical in every lane; lane 0 issues the copies)
-  long long vhead = 0, vtail = 0;
-  unsigned qh = 0, qt = 0;
+  // ring state (identical in every lane; lane 0 issues the copies); values
+  // streamed per sweep stay far below 2^32
+  unsigned vhead = 0, vtail = 0, qh = 0, qt = 0;
   int issue_k = 0;
 
   for (int sweep = 0; sweep < 2; ++sweep) {
@@ -594,7 +619,7 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
     auto produce = [&]() {
       while (issue_k < cnt && qh - qt < (unsigned)NQ) {
         int e = elem(issue_k);
-        int sz = seg_size(e);
+        unsigned sz = (unsigned)seg_size(e);
         if (sz == 0) {
           ++issue_k;
           continue;
@@ -603,15 +628,15 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
           vhead = (vhead + RINGV - 1) / RINGV * RINGV;
           vtail = vhead;
         }
-        long long pos = vhead % RINGV;
-        long long pad = (pos + sz > RINGV) ? RINGV - pos : 0;
-        if (vhead + pad + sz - vtail > RINGV) break;  // wait for the consumer to free space
+        unsigned pos = vhead % RINGV;
+        unsigned pad = (pos + sz > (unsigned)RINGV) ? RINGV - pos : 0;
+        if (vhead + pad + sz - vtail > (unsigned)RINGV) break;  // wait for the consumer to free space
         vhead += pad;
-        long long start = vhead;
+        unsigned start = vhead;
         vhead += sz;
         if (lane == 0) {
           qstart[qh % NQ] = start;
-          bulk_load(ring + start % RINGV, seg_src(e), (unsigned)(sz * sizeof(T)), &bars[qh % NQ]);
+          bulk_load(ring + start % RINGV, seg_src(e), sz * (unsigned)sizeof(T), &bars[qh % NQ]);
         }
         ++qh;
         ++issue_k;
@@ -627,66 +652,59 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
       if (sz) {
         unsigned q = qt % NQ;
         mbar_wait(&bars[q], (qt / NQ) & 1u, m.err_flag);
-        blk = ring + qstart[q] % RINGV;
+        blk = ring + (unsigned)qstart[q] % RINGV;
       }
-      if (sweep == 0) {
-        // y_i = r_i - sum_{lower k} L_ik y_k
-        unsigned low = m.lowmask[i];
-        int qb = 0;
-        for (int j = 0; j < DIM + 1; ++j) {
-          if (!((low >> j) & 1u)) continue;
-          int lk = m.nbr[j * ne + i] - base;
-          T d0 = (T)0, d1 = (T)0;
-          if (lane < NFR) {
+      const unsigned mask = sweep == 0 ? m.lowmask[i] : m.upmask[i];
+      // all block dot products first (independent), then the row updates in
+      // slot order (two facets of an element can share face rows)
+      T dj[DIM + 1];
 #pragma unroll
-            for (int c = 0; c < NED; c += 2) {
-              d0 += blk[qb * BS + c * NFR + lane] * ys[lk * NED + c];
-              d1 += blk[qb * BS + (c + 1) * NFR + lane] * ys[lk * NED + c + 1];
-            }
+      for (int j = 0; j < DIM + 1; ++j) {
+        dj[j] = (T)0;
+        if (((mask >> j) & 1u) && lane < NFR) {
+          const T* bq = blk + slots_below(mask, j) * BS + lane;
+          const T* yk = ys + (m.nbr[j * ne + i] - base) * NED;
+          T d0 = (T)0, d1 = (T)0, d2 = (T)0;
+#pragma unroll
+          for (int c = 0; c < NED; c += 3) {
+            d0 += bq[c * NFR] * yk[c];
+            d1 += bq[(c + 1) * NFR] * yk[c + 1];
+            d2 += bq[(c + 2) * NFR] * yk[c + 2];
           }
-          __syncwarp();
-          if (lane < NFR) ys[li * NED + face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= d0 + d1;
-          __syncwarp();
-          ++qb;
+          dj[j] = d0 + d1 + d2;
         }
-      } else {
-        // z_i = Dinv_i (y_i - sum_{upper j} U_ij z_j)
-        unsigned up = m.upmask[i];
+      }
+      T* target = sweep == 0 ? ys + li * NED : tmp;
+      if (sweep == 1) {
         if (lane < NED) tmp[lane] = ys[li * NED + lane];
-        __syncwarp();
-        int qb = 0;
-        for (int j = 0; j < DIM + 1; ++j) {
-          if (!((up >> j) & 1u)) continue;
-          int lk = m.nbr[j * ne + i] - base;
-          T d0 = (T)0, d1 = (T)0;
-          if (lane < NFR) {
+      }
+      __syncwarp();
 #pragma unroll
-            for (int c = 0; c < NED; c += 2) {
-              d0 += blk[qb * BS + c * NFR + lane] * ys[lk * NED + c];
-              d1 += blk[qb * BS + (c + 1) * NFR + lane] * ys[lk * NED + c + 1];
-            }
-          }
+      for (int j = 0; j < DIM + 1; ++j) {
+        if ((mask >> j) & 1u) {
+          if (lane < NFR) target[face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= dj[j];
           __syncwarp();
-          if (lane < NFR) tmp[face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= d0 + d1;
-          __syncwarp();
-          ++qb;
         }
-        const T* dinv = blk + qb * BS;
-        T z0 = (T)0, z1 = (T)0;
+      }
+      if (sweep == 1) {
+        // z_i = Dinv_i (y_i - sum_{upper j} U_ij z_j)
+        const T* dinv = blk + nbits(mask) * BS;
+        T z0 = (T)0, z1 = (T)0, z2 = (T)0;
         if (lane < NED) {
 #pragma unroll
-          for (int c = 0; c < NED; c += 2) {
+          for (int c = 0; c < NED; c += 3) {
             z0 += dinv[c * NED + lane] * tmp[c];
             z1 += dinv[(c + 1) * NED + lane] * tmp[c + 1];
+            z2 += dinv[(c + 2) * NED + lane] * tmp[c + 2];
           }
         }
         __syncwarp();
-        if (lane < NED) ys[li * NED + lane] = z0 + z1;
+        if (lane < NED) ys[li * NED + lane] = z0 + z1 + z2;
         __syncwarp();
       }
       if (sz) {
         ++qt;
-        vtail = (qt < qh) ? qstart[qt % NQ] : vhead;
+        vtail = (qt < qh) ? (unsigned)qstart[qt % NQ] : vhead;
       }
       produce();
     }
@@ -792,8 +810,17 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
   T acc[32];
 #pragma unroll
   for (int c = 0; c < 32; ++c) acc[c] = (T)0;
-  long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  for (long long iv = tid; iv < nv; iv += stride) {
+    VT wv = reinterpret_cast<const VT*>(w)[iv];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < ncols) acc[c] += Vec<T>::dot(reinterpret_cast<const VT*>(V + c * ldv)[iv], wv);
+  }
+  for (long long i = nv * VN + tid; i < n; i += stride) {
     T wv = w[i];
 #pragma unroll
     for (int c = 0; c < 32; ++c)
@@ -856,8 +883,19 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
   if (threadIdx.x < 32) h[threadIdx.x] = threadIdx.x < ncols ? (T)gs->H[j * 31 + threadIdx.x] : (T)0;
   __syncthreads();
   T acc_t = (T)0;
-  long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  for (long long iv = tid; iv < nv; iv += stride) {
+    VT ww = reinterpret_cast<const VT*>(w)[iv];
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < ncols) Vec<T>::axpy(ww, h[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
+    reinterpret_cast<VT*>(w)[iv] = ww;
+    acc_t += Vec<T>::dot(ww, ww);
+  }
+  for (long long i = nv * VN + tid; i < n; i += stride) {
     T ww = w[i];
 #pragma unroll
     for (int c = 0; c < 32; ++c)
@@ -896,8 +934,13 @@ template <typename T>
 __global__ void k_scale_into(const T* __restrict__ w, T* v, long long n, const double* s, const int* skip) {
   if (skip && *skip) return;
   T sc = (T)(*s);
-  long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) v[i] = w[i] * sc;
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  for (long long iv = tid; iv < nv; iv += stride)
+    reinterpret_cast<VT*>(v)[iv] = Vec<T>::scale(reinterpret_cast<const VT*>(w)[iv], sc);
+  for (long long i = nv * VN + tid; i < n; i += stride) v[i] = w[i] * sc;
 }
 
 __global__ void k_backsolve(GmresState* gs) {
@@ -917,8 +960,18 @@ __global__ void k_combine(const T* __restrict__ V, long long ldv, long long n, c
   int jl = gs->jlast;
   if (threadIdx.x < 32) y[threadIdx.x] = threadIdx.x < jl ? (T)gs->y[threadIdx.x] : (T)0;
   __syncthreads();
-  long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) {
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  for (long long iv = tid; iv < nv; iv += stride) {
+    VT s = Vec<T>::zero();
+#pragma unroll
+    for (int c = 0; c < 32; ++c)
+      if (c < jl) Vec<T>::fma(s, y[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
+    reinterpret_cast<VT*>(u)[iv] = s;
+  }
+  for (long long i = nv * VN + tid; i < n; i += stride) {
     T s = (T)0;
 #pragma unroll
     for (int c = 0; c < 32; ++c)
@@ -1061,6 +1114,15 @@ hf_status check_cuda(hf_mesh* h, cudaError_t e, const char* where) {
 // not captured in a graph; elapsed times are read at the next synchronisation.
 void prof_begin(hf_mesh* h, int kind) {
   Prof& p = h->prof;
+  if (p.capturing) {
+    if (p.graph_timing_error) return;
+    GraphEv g{kind, p.cap_j, nullptr, nullptr};
+    cudaEventCreate(&g.a);
+    cudaEventCreate(&g.b);
+    cudaEventRecord(g.a, h->stream);
+    p.cap_list->push_back(g);
+    return;
+  }
   if (!p.on) return;
   if (p.n >= PROF_EVENTS) prof_flush(h);
   if (!p.ev[2 * p.n]) {
@@ -1072,6 +1134,10 @@ void prof_begin(hf_mesh* h, int kind) {
 }
 void prof_end(hf_mesh* h) {
   Prof& p = h->prof;
+  if (p.capturing) {
+    if (!p.graph_timing_error) cudaEventRecord(p.cap_list->back().b, h->stream);
+    return;
+  }
   if (!p.on) return;
   cudaEventRecord(p.ev[2 * p.n + 1], h->stream);
   p.n += 1;
@@ -1087,6 +1153,26 @@ void prof_flush(hf_mesh* h) {
     p.launches[p.kind[i]] += 1;
   }
   p.n = 0;
+}
+
+// after a replay of a captured cycle that ran `iters` Arnoldi steps, add the
+// durations of the kernels those steps executed
+static void prof_flush_graph(hf_mesh* h, const std::vector<GraphEv>& ev, int iters) {
+  Prof& p = h->prof;
+  if (!p.on) return;
+  if (p.graph_timing_error) return;
+  for (const GraphEv& g : ev) {
+    if (g.j >= iters) continue;
+    float ms = 0.0f;
+    cudaError_t e = cudaEventElapsedTime(&ms, g.a, g.b);
+    if (e != cudaSuccess) {
+      cudaGetLastError();  // not sticky: clear it so later launch checks stay clean
+      p.graph_timing_error = (int)e;
+      return;
+    }
+    p.ms[g.kind] += ms;
+    p.launches[g.kind] += 1;
+  }
 }
 
 static int grid_for(long long n, int threads, int cap) {
@@ -1225,10 +1311,11 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
   GmresState* gs = h->d_gs;
   const int* done = &gs->done;
   long long N = h->N;
-  int rb = h->red_blocks;
+  int rb = 2 * 152;
   int* cnt = h->d_count + 4;
   for (int j = 0; j < mrest; ++j) {
     T* vj = K.V + (long long)j * K.ldv;
+    h->prof.cap_j = j;
     prof_begin(h, PK_PREC);
     precond<T, DIM>(h, K, vj, nullptr, nullptr, K.z, done);
     prof_end(h);
@@ -1248,19 +1335,26 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
 }
 
 template <typename T, int DIM>
-static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest, cudaGraphExec_t* gexec) {
+static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest, cudaGraphExec_t* gexec,
+                           std::vector<GraphEv>* gev) {
   if (!h->opts.use_graphs) {
     gmres_cycle<T, DIM>(h, K, dg, off, mrest);
     return HF_OK;
   }
   if (!*gexec) {
+    for (GraphEv& g : *gev) {
+      cudaEventDestroy(g.a);
+      cudaEventDestroy(g.b);
+    }
+    gev->clear();
     cudaGraph_t g;
     cudaError_t e = cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeThreadLocal);
     if (e != cudaSuccess) return check_cuda(h, e, "cudaStreamBeginCapture");
-    bool pon = h->prof.on;
-    h->prof.on = false;
+    h->prof.capturing = true;
+    h->prof.cap_list = gev;
     gmres_cycle<T, DIM>(h, K, dg, off, mrest);
-    h->prof.on = pon;
+    h->prof.capturing = false;
+    h->prof.cap_list = nullptr;
     e = cudaStreamEndCapture(h->stream, &g);
     if (e != cudaSuccess) return check_cuda(h, e, "cudaStreamEndCapture");
     e = cudaGraphInstantiate(gexec, g, 0);
@@ -1332,8 +1426,9 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
         break;
       }
       if (rnorm <= tol || total >= o.max_iters) break;
-      if ((st = run_cycle<double, DIM>(h, K, h->J64.dg, h->J64.off, mrest, &h->graph64))) break;
+      if ((st = run_cycle<double, DIM>(h, K, h->J64.dg, h->J64.off, mrest, &h->graph64, &h->gev64))) break;
       if ((st = read_gs(h, &ci))) break;
+      if (o.use_graphs) prof_flush_graph(h, h->gev64, ci.iters);
       total += ci.iters;
     }
     cudaMemcpyAsync(x, K.x, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
@@ -1358,9 +1453,10 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
       { note_launch(); k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs, o.inner_rtol); }
       { note_launch(); k_scale_into<float><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
       cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
-      if ((st = run_cycle<float, DIM>(h, K, h->J32.dg, h->J32.off, mrest, &h->graph32))) break;
+      if ((st = run_cycle<float, DIM>(h, K, h->J32.dg, h->J32.off, mrest, &h->graph32, &h->gev32))) break;
       CycleInfo ci;
       if ((st = read_gs(h, &ci))) break;
+      if (o.use_graphs) prof_flush_graph(h, h->gev32, ci.iters);
       total += ci.iters;
       refinements += 1;
       { note_launch(); k_promote_axpy<<<rb, RB, 0, h->stream>>>(x, K.x, N, h->d_red); }

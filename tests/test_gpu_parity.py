@@ -76,12 +76,13 @@ def test_criterion_traction_parity(name):
     g.close()
 
 
-@pytest.mark.parametrize("name,prec,tol", [("2d_midline", "fp64", 1e-10), ("2d_all", "fp64", 1e-10),
-                                           ("3d_plane", "fp64", 1e-10), ("3d_all", "fp64", 1e-10),
-                                           ("2d_midline", "mixed", 1e-8), ("3d_all", "mixed", 1e-8)])
-def test_newton_step_parity(name, prec, tol):
+@pytest.mark.parametrize("name,prec,tol,graphs", [("2d_midline", "fp64", 1e-10, 0), ("2d_all", "fp64", 1e-10, 0),
+                                                  ("3d_plane", "fp64", 1e-10, 0), ("3d_all", "fp64", 1e-10, 0),
+                                                  ("2d_midline", "mixed", 1e-8, 0), ("3d_all", "mixed", 1e-8, 0),
+                                                  ("3d_all", "fp64", 1e-10, 1), ("3d_all", "mixed", 1e-8, 1)])
+def test_newton_step_parity(name, prec, tol, graphs):
     wl = cases()[name]
-    o, g, _ = _pair(wl, precision=prec, rtol=1e-13 if prec == "fp64" else 1e-11)
+    o, g, _ = _pair(wl, precision=prec, rtol=1e-13 if prec == "fp64" else 1e-11, use_graphs=graphs)
     rep = g.hf_newton_step()
     o.newton_step()
     Ug, Pg = g.hf_get_state()[:2]
