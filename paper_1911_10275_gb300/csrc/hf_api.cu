@@ -341,9 +341,33 @@ static hf_status build_subdomains(hf_mesh* h, int G) {
       off += __builtin_popcount((unsigned)up[e]) * bs + dsz;
     }
   }
+  // per position in level order: local element id, lower/upper slot masks and
+  // the local ids of the four slot neighbours (255 outside the subdomain)
+  std::vector<unsigned char> task((size_t)ne * 8, 255);
+  std::vector<long long> sd_fwd(nsd), sd_bwd(nsd);
+  for (int s = 0; s < nsd; ++s) {
+    int b = s * G, c = std::min(G, ne - b);
+    for (int k = 0; k < c; ++k) {
+      int e = sd_elems[b + k];
+      unsigned char* t = &task[(size_t)(b + k) * 8];
+      t[0] = (unsigned char)(e - b);
+      t[1] = low[e];
+      t[2] = up[e];
+      for (int j = 0; j < nsl; ++j) {
+        int nb = h->h_nbr[j * ne + e];
+        t[4 + j] = (nb >= b && nb < b + c) ? (unsigned char)(nb - b) : 255;
+      }
+    }
+    sd_fwd[s] = c ? rec_fwd[sd_elems[b]] : 0;
+    sd_bwd[s] = c ? rec_bwd[sd_elems[b + c - 1]] : 0;
+  }
   h->d.rec_fwd = upload(h, rec_fwd);
   h->d.rec_bwd = upload(h, rec_bwd);
-  if (!h->d.rec_fwd || !h->d.rec_bwd) return set_error(h, HF_ERR_OOM, "ILU record offsets");
+  h->d.sd_task = upload(h, task);
+  h->d.sd_fwd = upload(h, sd_fwd);
+  h->d.sd_bwd = upload(h, sd_bwd);
+  if (!h->d.rec_fwd || !h->d.rec_bwd || !h->d.sd_task || !h->d.sd_fwd || !h->d.sd_bwd)
+    return set_error(h, HF_ERR_OOM, "ILU record offsets");
   return check_cuda(h, cudaGetLastError(), "build_subdomains");
 }
 

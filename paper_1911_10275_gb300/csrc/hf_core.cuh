@@ -144,6 +144,9 @@ struct DevMesh {
   int* sd_nlvl;             // [nsd]
   long long* rec_fwd;       // [ne] start of the element's forward segment (L blocks)
   long long* rec_bwd;       // [ne] start of the element's backward segment (U blocks, Dinv)
+  unsigned char* sd_task;   // [8 per position in level order]: local id, lower mask, upper mask, -, 4 local nbrs
+  long long* sd_fwd;        // [nsd] start of each subdomain's forward stream
+  long long* sd_bwd;        // [nsd] start of each subdomain's backward stream
   int* err_flag;            // [0]: a bounded wait in a kernel gave up
   // parameters
   double lam, mu, sigma_c, delta_c, b_stab;

@@ -148,6 +148,7 @@ struct hf_mesh {
   // CUDA graphs of one GMRES cycle per precision
   cudaGraphExec_t graph64 = nullptr, graph32 = nullptr;
   std::vector<hfk::GraphEv> gev64, gev32;  // timing events baked into the graphs
+  long long graph_kernels64 = 0, graph_kernels32 = 0;  // kernel nodes per captured cycle
   hfk::Prof prof;
   long long n_interior_slots = 0, n_subdomain_slots = 0;
 };

@@ -585,41 +585,43 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
   if (skip && *skip) return;
   extern __shared__ __align__(128) unsigned char smraw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // per-warp region: ring | ys | tmp | queue starts | barriers
+  // per-warp region: ring | ys | tmp | queue starts | barriers | task table
   const size_t per_warp =
-      ((size_t)(RINGV + m.G * NED + 32) * sizeof(T) + NQ * sizeof(long long) + NQ * 8 + 127) / 128 * 128;
+      ((size_t)(RINGV + m.G * NED + 32) * sizeof(T) + NQ * sizeof(long long) + NQ * 8 + (size_t)m.G * 8 + 127) /
+      128 * 128;
   unsigned char* region = smraw + (size_t)warp * per_warp;
   T* ring = reinterpret_cast<T*>(region);
   T* ys = ring + RINGV;
   T* tmp = ys + (size_t)m.G * NED;
   long long* qstart = reinterpret_cast<long long*>(tmp + 32);
   unsigned long long* bars = reinterpret_cast<unsigned long long*>(qstart + NQ);
+  unsigned char* task = reinterpret_cast<unsigned char*>(bars + NQ);
   if (lane < NQ) mbar_init(&bars[lane], 1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   __syncthreads();
   const int s = blockIdx.x * W + warp;
   if (s >= m.nsd) return;
   const int base = s * m.G, cnt = min(m.G, m.ne - base);
-  const long long ne = m.ne;
   for (int t = lane; t < cnt * NED; t += 32) ys[t] = rin[(long long)base * NED + t];
+  for (int t = lane; t < cnt * 2; t += 32)
+    reinterpret_cast<unsigned*>(task)[t] = reinterpret_cast<const unsigned*>(m.sd_task + (size_t)base * 8)[t];
+  // face row of this lane in each facet slot
+  int frow[DIM + 1];
+#pragma unroll
+  for (int j = 0; j < DIM + 1; ++j) frow[j] = face_node<DIM>(j, (lane < NFR ? lane : 0) / DIM) * DIM + lane % DIM;
   __syncwarp();
-  const int* order = m.sd_elems + base;  // level order
-  // ring state (identical in every lane; lane 0 issues the copies); values
-  // streamed per sweep stay far below 2^32
   unsigned vhead = 0, vtail = 0, qh = 0, qt = 0;
-  int issue_k = 0;
 
   for (int sweep = 0; sweep < 2; ++sweep) {
-    issue_k = 0;
-    auto elem = [&](int k) { return sweep == 0 ? order[k] : order[cnt - 1 - k]; };
-    auto seg_size = [&](int e) -> int {
-      return sweep == 0 ? nbits(m.lowmask[e]) * BS : nbits(m.upmask[e]) * BS + NED * NED;
+    int issue_k = 0;
+    const T* src = lu + (sweep == 0 ? m.sd_fwd[s] : m.sd_bwd[s]);  // stream cursor
+    auto tk = [&](int k) -> const unsigned char* { return task + 8 * (sweep == 0 ? k : cnt - 1 - k); };
+    auto seg_size = [&](const unsigned char* t) -> unsigned {
+      return sweep == 0 ? nbits(t[1]) * BS : nbits(t[2]) * BS + NED * NED;
     };
-    auto seg_src = [&](int e) -> const T* { return lu + (sweep == 0 ? m.rec_fwd[e] : m.rec_bwd[e]); };
     auto produce = [&]() {
       while (issue_k < cnt && qh - qt < (unsigned)NQ) {
-        int e = elem(issue_k);
-        unsigned sz = (unsigned)seg_size(e);
+        unsigned sz = seg_size(tk(issue_k));
         if (sz == 0) {
           ++issue_k;
           continue;
@@ -636,8 +638,9 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
         vhead += sz;
         if (lane == 0) {
           qstart[qh % NQ] = start;
-          bulk_load(ring + start % RINGV, seg_src(e), sz * (unsigned)sizeof(T), &bars[qh % NQ]);
+          bulk_load(ring + start % RINGV, src, sz * (unsigned)sizeof(T), &bars[qh % NQ]);
         }
+        src += sz;
         ++qh;
         ++issue_k;
       }
@@ -645,16 +648,16 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
     };
     produce();
     for (int k = 0; k < cnt; ++k) {
-      int i = elem(k);
-      int li = i - base;
-      int sz = seg_size(i);
+      const unsigned char* t = tk(k);
+      const int li = t[0];
+      const unsigned mask = sweep == 0 ? t[1] : t[2];
+      const unsigned sz = seg_size(t);
       const T* blk = nullptr;
       if (sz) {
         unsigned q = qt % NQ;
         mbar_wait(&bars[q], (qt / NQ) & 1u, m.err_flag);
         blk = ring + (unsigned)qstart[q] % RINGV;
       }
-      const unsigned mask = sweep == 0 ? m.lowmask[i] : m.upmask[i];
       // all block dot products first (independent), then the row updates in
       // slot order (two facets of an element can share face rows)
       T dj[DIM + 1];
@@ -663,7 +666,7 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
         dj[j] = (T)0;
         if (((mask >> j) & 1u) && lane < NFR) {
           const T* bq = blk + slots_below(mask, j) * BS + lane;
-          const T* yk = ys + (m.nbr[j * ne + i] - base) * NED;
+          const T* yk = ys + t[4 + j] * NED;
           T d0 = (T)0, d1 = (T)0, d2 = (T)0;
 #pragma unroll
           for (int c = 0; c < NED; c += 3) {
@@ -675,14 +678,12 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
         }
       }
       T* target = sweep == 0 ? ys + li * NED : tmp;
-      if (sweep == 1) {
-        if (lane < NED) tmp[lane] = ys[li * NED + lane];
-      }
+      if (sweep == 1 && lane < NED) tmp[lane] = ys[li * NED + lane];
       __syncwarp();
 #pragma unroll
       for (int j = 0; j < DIM + 1; ++j) {
         if ((mask >> j) & 1u) {
-          if (lane < NFR) target[face_node<DIM>(j, lane / DIM) * DIM + lane % DIM] -= dj[j];
+          if (lane < NFR) target[frow[j]] -= dj[j];
           __syncwarp();
         }
       }
@@ -1276,7 +1277,9 @@ static void spmv(hf_mesh* h, const T* dg, const T* off, const T* x, T* y, const 
 template <int DIM, typename T> static size_t apply_smem(int G, int W) {
   using S = Shape<DIM>;
   size_t per_warp =
-      ((size_t)(ApplyRing<T, DIM>::RINGV + G * S::ned + 32) * sizeof(T) + APPLY_NQ * 8 + APPLY_NQ * 8 + 127) / 128 * 128;
+      ((size_t)(ApplyRing<T, DIM>::RINGV + G * S::ned + 32) * sizeof(T) + APPLY_NQ * 8 + APPLY_NQ * 8 + (size_t)G * 8 +
+       127) /
+      128 * 128;
   return (size_t)W * per_warp;
 }
 
@@ -1337,6 +1340,7 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
 template <typename T, int DIM>
 static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest, cudaGraphExec_t* gexec,
                            std::vector<GraphEv>* gev) {
+  long long& gk = sizeof(T) == 8 ? h->graph_kernels64 : h->graph_kernels32;
   if (!h->opts.use_graphs) {
     gmres_cycle<T, DIM>(h, K, dg, off, mrest);
     return HF_OK;
@@ -1352,7 +1356,10 @@ static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, 
     if (e != cudaSuccess) return check_cuda(h, e, "cudaStreamBeginCapture");
     h->prof.capturing = true;
     h->prof.cap_list = gev;
+    long long before = launch_counter();
     gmres_cycle<T, DIM>(h, K, dg, off, mrest);
+    gk = launch_counter() - before;  // kernel nodes of the graph, counted per replay
+    launch_counter() = before;
     h->prof.capturing = false;
     h->prof.cap_list = nullptr;
     e = cudaStreamEndCapture(h->stream, &g);
@@ -1361,6 +1368,7 @@ static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, 
     cudaGraphDestroy(g);
     if (e != cudaSuccess) return check_cuda(h, e, "cudaGraphInstantiate");
   }
+  launch_counter() += gk;
   return check_cuda(h, cudaGraphLaunch(*gexec, h->stream), "cudaGraphLaunch");
 }
 
