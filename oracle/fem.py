@@ -447,11 +447,28 @@ class Oracle:
             self.c_scale = 1.0
 
     # ---------------------------------------------------------------- assembly
-    def assemble(self, U=None, P=None, with_jacobian=True):
+    def assemble(self, U=None, P=None, with_jacobian=True, elems=None, pdofs=None):
         """Residual R(U, P) and Jacobian J = dR/d(U, P) in natural DOF order
-        (displacements element-major, then pressures)."""
+        (displacements element-major, then pressures).
+
+        With ``elems`` / ``pdofs`` given, only those elements and the facets
+        touching them or those pressure DOFs are visited: the rows of the
+        listed elements and pressure DOFs are then exact and every other row
+        is partial (used to check sampled rows of a large problem)."""
         U = self.U if U is None else U
         P = self.P if P is None else P
+        sample = elems is not None or pdofs is not None
+        if sample:
+            elem_list = np.asarray(elems if elems is not None else [], dtype=np.int64)
+            want_p = set(int(g) for g in (pdofs if pdofs is not None else []))
+            touch = set(int(e) for e in elem_list)
+            face_list = [f for f in range(self.nf)
+                         if int(self.m.face_elems[f, 0]) in touch or int(self.m.face_elems[f, 1]) in touch
+                         or (self.m.face_crackable[f] and
+                             any(self.pindex[int(g)] in want_p for g in self.fnodes[f]))]
+        else:
+            elem_list = range(self.ne)
+            face_list = range(self.nf)
         p = self.prm
         d, ned = self.dim, self.ned
         R = np.zeros(self.N)
@@ -464,7 +481,7 @@ class Oracle:
             vals.append(v.ravel())
 
         # bulk elasticity
-        for e in range(self.ne):
+        for e in elem_list:
             Ke = self.element_stiffness(e)
             dofs = self.udofs(e)
             R[dofs] += Ke @ U[dofs]
@@ -473,7 +490,7 @@ class Oracle:
         # interior facets
         act = self.active_pdofs()
         c = self.c_scale
-        for f in range(self.nf):
+        for f in face_list:
             if self.m.face_elems[f, 1] < 0:
                 continue
             sides = self._side(f)
@@ -524,6 +541,8 @@ class Oracle:
                     add(pdofs, pdofs, c * np.einsum("q,q,qgi,qhi->gh", wq, k3, geta, geta))
         # Neumann traction on outer facets
         for f, tb in zip(self.neu_faces, self.neu_traction):
+            if sample and int(self.m.face_elems[f, 0]) not in touch:
+                continue
             e = int(self.m.face_elems[f, 0])
             x, wq = self.face_points(f)
             N, _ = self.elem_basis_at(e, x)

@@ -419,3 +419,22 @@ def test_beta_activation_and_opening_roll():
         assert o.beta[f] == expect
         assert np.allclose(o.w_old[f], w0, rtol=1e-12)
         assert o.t == pytest.approx(1.25)
+
+
+def test_sampled_assembly_rows_equal_global_rows():
+    """The sampled assembly used for large-problem checks reproduces, on its
+    listed rows, the global residual and Jacobian exactly."""
+    m, o = _kgd_setup(n=6, L=12.0)
+    al = o.alpha.copy()
+    cr = np.nonzero(m.face_crackable & (o.alpha == 0))[0]
+    al[cr[:1]] = 1
+    o.set_state(o.U, o.P, al, o.beta, w_old=o.w_old)
+    R, J = o.assemble()
+    rng = np.random.default_rng(11)
+    elems = rng.choice(o.ne, size=7, replace=False)
+    pd = rng.choice(np.nonzero(o.active_pdofs())[0], size=3, replace=False)
+    Rs, Js = o.assemble(elems=elems, pdofs=pd)
+    rows = np.concatenate([np.concatenate([o.udofs(e) for e in elems]), o.Nu + pd])
+    assert np.array_equal(Rs[rows], R[rows])
+    x = rng.standard_normal(o.N)
+    assert np.allclose((Js @ x)[rows], (J @ x)[rows], rtol=1e-14, atol=0)
