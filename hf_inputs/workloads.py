@@ -6,10 +6,11 @@ delta_c / 2 (the relation stated beside Eq. tsl) with G_c = K_Ic^2 / E'."""
 from __future__ import annotations
 
 import dataclasses
+import math
 
 import numpy as np
 
-from .mesh import Mesh, square_p2, cube_p2, pressure_nodes, seed_state
+from .mesh import Mesh, square_p2, cube_p2, pressure_nodes, seed_state, batch_instances
 
 
 @dataclasses.dataclass
@@ -85,3 +86,74 @@ def c3_penny():
     """The penny crack lives in its plane z = 0, as the KGD crack lives on the
     midline: facets off the plane are intact DG interfaces."""
     return penny_3d(n=18, crackable="plane", name="c3_penny3d_n18_mixed")
+
+
+# ---------------------------------------------------------------- many instances
+def _even(x, lo, hi):
+    n = int(round(x / 2.0)) * 2
+    return max(lo, min(hi, n))
+
+
+def _log_uniform(rng, lo, hi):
+    return float(math.exp(rng.uniform(math.log(lo), math.log(hi))))
+
+
+def sample_parameters(rng):
+    """E, K_Ic, mu, Q0 drawn log-uniformly over the ranges of the batched
+    sweep: E in [5, 50] GPa, K_Ic in [0.1, 3] MPa m^1/2, mu in [1e-3, 1] Pa s,
+    Q0 in [1e-4, 1e-2] (m^2/s in 2D, m^3/s in 3D)."""
+    return {"E": _log_uniform(rng, 5e9, 50e9), "K_Ic": _log_uniform(rng, 0.1e6, 3e6),
+            "mu": _log_uniform(rng, 1e-3, 1.0), "Q0": _log_uniform(rng, 1e-4, 1e-2)}
+
+
+def sweep_instances(count=256, seed=191110275, ne_range=(1000, 50000), steps=10, mesh_cache=None):
+    """Batched 2D KGD sweep: `count` independent plane-strain instances with
+    the draws of batch_instances (element count, E, K_Ic, mu, Q0 log-uniform),
+    nu = 0.2, sigma_c = 1 MPa, crack on the midline.  Meshes of equal n are
+    shared through mesh_cache (a dict)."""
+    cache = {} if mesh_cache is None else mesh_cache
+    out = []
+    for i, d in enumerate(batch_instances(count, seed, ne_range)):
+        n = d["n"]
+        key = ("kgd", n)
+        if key not in cache:
+            cache[key] = square_p2(n, 100.0, crackable="midline")
+        h = 100.0 / n
+        out.append(Workload(f"sweep{i}_kgd2d_n{n}", cache[key], d["E"], 0.2, d["K_Ic"], 1e6, d["mu"], d["Q0"], 1.0,
+                            steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6))
+    return out
+
+
+def serving_requests(count=2000, rate=200.0, seed=191110275, kgd_n=(50, 316), penny_n=(7, 22), steps=5,
+                     mesh_cache=None):
+    """Poisson stream of solve requests: exponential inter-arrival times of
+    mean 1/rate, half plane-strain KGD (n x n squares of two P2 triangles,
+    n in kgd_n), half penny-shaped (n^3 cubes of six P2 tetrahedra, n in
+    penny_n, crack plane z = 0), parameters from sample_parameters (nu = 0.2
+    for KGD, 0.25 for the penny), `steps` time steps each from the seed
+    state.  sigma_c is 1 MPa for KGD and 0.3 MPa for the penny (a cohesive
+    length spanning several tetrahedra, as in the penny benchmark).  Returns
+    (arrival times in s, workloads)."""
+    rng = np.random.default_rng(seed)
+    cache = {} if mesh_cache is None else mesh_cache
+    t = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    out = []
+    for i in range(count):
+        prm = sample_parameters(rng)
+        if rng.uniform() < 0.5:
+            n = _even(math.exp(rng.uniform(math.log(kgd_n[0]), math.log(kgd_n[1]))), kgd_n[0], kgd_n[1])
+            key = ("kgd", n)
+            if key not in cache:
+                cache[key] = square_p2(n, 100.0, crackable="midline")
+            h = 100.0 / n
+            out.append(Workload(f"req{i}_kgd2d_n{n}", cache[key], prm["E"], 0.2, prm["K_Ic"], 1e6, prm["mu"],
+                                prm["Q0"], 1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6))
+        else:
+            n = _even(math.exp(rng.uniform(math.log(penny_n[0]), math.log(penny_n[1]))), penny_n[0] + 1, penny_n[1])
+            key = ("penny", n)
+            if key not in cache:
+                cache[key] = cube_p2(n, 50.0, crackable="plane")
+            h = 50.0 / n
+            out.append(Workload(f"req{i}_penny3d_n{n}", cache[key], prm["E"], 0.25, prm["K_Ic"], 0.3e6, prm["mu"],
+                                prm["Q0"], 1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=2e-3, p0=1e6))
+    return t, out

@@ -203,7 +203,7 @@ hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
  * unknowns, [7] facets, [8] kernel launches issued by the library in this
  * process so far, [9] CUDA error met when reading timing events recorded
  * inside a captured GMRES cycle (0: none; graph cycles then go untimed),
- * [10..15] zero.  st holds 16. */
+ * [10] device bytes the handle holds, [11..15] zero.  st holds 16. */
 hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
 
 const char* hf_last_error(const hf_mesh* h);
@@ -230,6 +230,127 @@ const char* hf_last_error(const hf_mesh* h);
  * (may be NULL) receives a message of at most err_len bytes. */
 hf_status hf_increment_norms_noalloc(const double* d_dx, const double* d_x, int64_t n_u, int64_t n_p,
                                      double* d_out, void* cuda_stream, char* err, int64_t err_len);
+
+/* ------------------------------------------------------------ time step */
+
+/* Options of hf_advance_step. */
+typedef struct {
+  int newton_max;        /* Newton iterations per attempt before the step is cut (default 8) */
+  int criterion_rounds;  /* criterion / Newton-again rounds per sub-step (default 4) */
+  int max_cutbacks;      /* halvings of the sub-step before the call gives up (default 10) */
+} hf_step_opts;
+
+typedef struct {
+  int64_t newton_iters;  /* Newton iterations, failed attempts included */
+  int64_t gmres_iters;   /* Arnoldi iterations over those Newton iterations */
+  int64_t substeps;      /* accepted sub-steps (1 when the full step converged) */
+  int64_t cutbacks;      /* attempts undone and halved */
+  int64_t new_alpha;     /* facets switched to cohesive */
+  int64_t new_beta;      /* facets switched to fluid-filled */
+  double t;              /* time reached (t + dt on success) */
+  double du_rel, dp_rel; /* relative increments of the last Newton iteration */
+} hf_step_report;
+
+void hf_default_step_opts(hf_step_opts* o);
+
+/* One time step of length dt (hf_set_injection) as Sec. 3 drives it: Newton
+ * iterations (hf_newton_step) until the relative increments meet the
+ * tolerance, then the fracture criterion; if it switched facets, Newton
+ * again (at most criterion_rounds rounds); then the end of the step
+ * (hf_accept_step).  An attempt that does not converge within newton_max
+ * iterations, whose linear solve does not converge, or whose state turns
+ * non-finite is undone from a device copy of the start-of-step state and
+ * retried with half the sub-step; after a success the sub-step grows by 1.5
+ * up to dt, until t + dt is reached.  dt itself is left unchanged.  Errors:
+ * HF_ERR_NOT_CONVERGED after max_cutbacks halvings (state = the last accepted
+ * sub-step), any CUDA or state error as returned by the calls above. */
+hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* rep);
+
+/* Unknown counts of the system a descriptor defines, without a handle:
+ * n_u = n_elems * nen * dim displacements, n_p pressure unknowns (the
+ * distinct nodes of crackable interior facets). */
+hf_status hf_mesh_sizes(const hf_mesh_desc* desc, int64_t* n_u, int64_t* n_p);
+
+/* Upper bound on the device memory a handle for this mesh holds once it has
+ * been created and stepped with the given Jacobi block size (both solver
+ * precisions, the step snapshot included); read with hf_get_stats [10]. */
+hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, int jacobi_block, int64_t* bytes);
+
+/* ------------------------------------------------------------ serving */
+
+/* A request loop over many independent fracture problems.  The paper solves
+ * one problem at a time; this runtime keeps several on the device at once.
+ * `slots` worker threads each own a CUDA stream; a submitted request waits
+ * in a FIFO queue until a slot is free and its device-memory bound
+ * (hf_estimate_device_bytes) fits in what the budget has left; smaller
+ * requests may pass a waiting larger one at most `max_bypass` times.  An
+ * admitted request builds its handle on the slot's stream, runs n_steps calls
+ * of hf_advance_step with its mesh, state, crack state and Krylov workspace
+ * resident, copies its final state to host memory and frees its device
+ * memory.  Requests on different slots overlap on the GPU. */
+typedef struct hf_runtime hf_runtime;
+
+typedef struct {
+  int slots;                 /* concurrent requests (1..64) */
+  int64_t hbm_budget_bytes;  /* bound on the summed estimates of admitted requests */
+  int max_bypass;            /* times the head of the queue may be passed (default 8) */
+  int device;                /* CUDA device ordinal */
+} hf_runtime_opts;
+
+/* A request: every array is host memory owned by the caller and copied by
+ * hf_runtime_submit.  Material, injection and solver options as in
+ * hf_set_material / hf_set_injection / hf_set_solver; the initial state as in
+ * hf_set_state (NULL U0, P0, alpha0, beta0: zeros). */
+typedef struct {
+  const hf_mesh_desc* mesh;
+  double E, nu, sigma_c, delta_c, b_stab;
+  double mu, Q0;
+  int64_t n_inj;
+  const int64_t* inj_dofs;
+  const double* inj_weights;
+  double delta_f, dt, p_vapor;
+  int cutoff_on;
+  double L_ref;
+  hf_solver_opts solver;
+  hf_step_opts step;
+  int n_steps;
+  const double* U0;
+  const double* P0;
+  const int8_t* alpha0;
+  const int8_t* beta0;
+  double t0;
+} hf_request;
+
+typedef struct {
+  hf_status status;        /* HF_OK, or the first error of the request */
+  int64_t n_u, n_p, n_faces;
+  int64_t steps_done;
+  int64_t newton_iters, gmres_iters, cutbacks;
+  int64_t device_bytes;    /* the handle's device memory after its last step */
+  int64_t estimate_bytes;  /* the bound admission used */
+  double t_submit, t_admit, t_done;  /* seconds on the runtime's clock */
+  double t_final;          /* simulated time reached */
+} hf_result;
+
+hf_status hf_runtime_create(const hf_runtime_opts* opts, hf_runtime** out);
+/* Waits for running requests, drops queued ones, joins the workers. */
+hf_status hf_runtime_destroy(hf_runtime* rt);
+/* Queues a copy of the request; *id identifies it. HF_ERR_INVALID_ARG on a
+ * malformed request; one whose estimate exceeds the budget completes at once
+ * with status HF_ERR_OOM. */
+hf_status hf_runtime_submit(hf_runtime* rt, const hf_request* req, int64_t* id);
+/* Waits up to timeout_s seconds (< 0: without limit) for request id to
+ * finish and fills *res; HF_ERR_TIMEOUT if it has not finished by then. */
+hf_status hf_runtime_wait(hf_runtime* rt, int64_t id, double timeout_s, hf_result* res);
+/* Copies the final state of a finished request (sizes from hf_result; any
+ * pointer may be NULL) and forgets the request. */
+hf_status hf_runtime_fetch(hf_runtime* rt, int64_t id, double* U, double* P, int8_t* alpha, int8_t* beta);
+/* [0] queued, [1] running, [2] finished and not fetched, [3] device bytes
+ * admitted now, [4] peak admitted bytes, [5] peak running requests,
+ * [6] requests completed so far, [7] requests that failed.  st holds 8. */
+hf_status hf_runtime_stats(hf_runtime* rt, int64_t* st);
+/* Seconds since hf_runtime_create on the runtime's clock. */
+double hf_runtime_now(const hf_runtime* rt);
 
 #ifdef __cplusplus
 }

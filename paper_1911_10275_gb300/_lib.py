@@ -46,6 +46,45 @@ class hf_newton_report(C.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class hf_step_opts(C.Structure):
+    _fields_ = [("newton_max", C.c_int), ("criterion_rounds", C.c_int), ("max_cutbacks", C.c_int)]
+
+
+class hf_step_report(C.Structure):
+    _fields_ = [("newton_iters", C.c_int64), ("gmres_iters", C.c_int64), ("substeps", C.c_int64),
+                ("cutbacks", C.c_int64), ("new_alpha", C.c_int64), ("new_beta", C.c_int64),
+                ("t", C.c_double), ("du_rel", C.c_double), ("dp_rel", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class hf_runtime_opts(C.Structure):
+    _fields_ = [("slots", C.c_int), ("hbm_budget_bytes", C.c_int64), ("max_bypass", C.c_int), ("device", C.c_int)]
+
+
+class hf_request(C.Structure):
+    _fields_ = [("mesh", C.POINTER(hf_mesh_desc)),
+                ("E", C.c_double), ("nu", C.c_double), ("sigma_c", C.c_double), ("delta_c", C.c_double),
+                ("b_stab", C.c_double), ("mu", C.c_double), ("Q0", C.c_double),
+                ("n_inj", C.c_int64), ("inj_dofs", _i64p), ("inj_weights", _dp),
+                ("delta_f", C.c_double), ("dt", C.c_double), ("p_vapor", C.c_double),
+                ("cutoff_on", C.c_int), ("L_ref", C.c_double),
+                ("solver", hf_solver_opts), ("step", hf_step_opts), ("n_steps", C.c_int),
+                ("U0", _dp), ("P0", _dp), ("alpha0", _i8p), ("beta0", _i8p), ("t0", C.c_double)]
+
+
+class hf_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("n_u", C.c_int64), ("n_p", C.c_int64), ("n_faces", C.c_int64),
+                ("steps_done", C.c_int64), ("newton_iters", C.c_int64), ("gmres_iters", C.c_int64),
+                ("cutbacks", C.c_int64), ("device_bytes", C.c_int64), ("estimate_bytes", C.c_int64),
+                ("t_submit", C.c_double), ("t_admit", C.c_double), ("t_done", C.c_double),
+                ("t_final", C.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
 _H = C.c_void_p
 SIGNATURES = {
     "hf_default_solver_opts": (None, [C.POINTER(hf_solver_opts)]),
@@ -73,6 +112,17 @@ SIGNATURES = {
     "hf_last_error": (C.c_char_p, [_H]),
     "hf_increment_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int64, C.c_int64, C.c_void_p,
                                              C.c_void_p, C.c_char_p, C.c_int64]),
+    "hf_default_step_opts": (None, [C.POINTER(hf_step_opts)]),
+    "hf_advance_step": (C.c_int, [_H, C.POINTER(hf_step_opts), C.POINTER(hf_step_report)]),
+    "hf_mesh_sizes": (C.c_int, [C.POINTER(hf_mesh_desc), _i64p, _i64p]),
+    "hf_estimate_device_bytes": (C.c_int, [C.POINTER(hf_mesh_desc), C.c_int, _i64p]),
+    "hf_runtime_create": (C.c_int, [C.POINTER(hf_runtime_opts), C.POINTER(C.c_void_p)]),
+    "hf_runtime_destroy": (C.c_int, [C.c_void_p]),
+    "hf_runtime_submit": (C.c_int, [C.c_void_p, C.POINTER(hf_request), _i64p]),
+    "hf_runtime_wait": (C.c_int, [C.c_void_p, C.c_int64, C.c_double, C.POINTER(hf_result)]),
+    "hf_runtime_fetch": (C.c_int, [C.c_void_p, C.c_int64, _dp, _dp, _i8p, _i8p]),
+    "hf_runtime_stats": (C.c_int, [C.c_void_p, _i64p]),
+    "hf_runtime_now": (C.c_double, [C.c_void_p]),
 }
 KERNEL_CLASSES = ["spmv", "precond", "orth", "factor", "assembly", "spmv64", "update", "unused"]
 
@@ -108,27 +158,79 @@ class HFError(RuntimeError):
         self.status = status
 
 
+def make_desc(dim, xyz, elem_nodes, face_elems, face_local, face_crackable, dir_dof, dir_val,
+              neu_face=None, neu_traction=None):
+    """hf_mesh_desc over contiguous copies of the arrays; returns (desc, keep),
+    where keep owns the memory the descriptor points into."""
+    keep = [np.ascontiguousarray(xyz, dtype=np.float64),
+            np.ascontiguousarray(elem_nodes, dtype=np.int32),
+            np.ascontiguousarray(face_elems, dtype=np.int32),
+            np.ascontiguousarray(face_local, dtype=np.int8),
+            np.ascontiguousarray(face_crackable, dtype=np.int8),
+            np.ascontiguousarray(dir_dof, dtype=np.int64),
+            np.ascontiguousarray(dir_val, dtype=np.float64),
+            np.ascontiguousarray(neu_face if neu_face is not None else np.zeros(0), dtype=np.int32),
+            np.ascontiguousarray(neu_traction if neu_traction is not None else np.zeros(0), dtype=np.float64)]
+    x, en, fe, fl, fc, dd, dv, nf_, nt = keep
+    d = hf_mesh_desc(dim, 2, x.shape[0], _ptr(x, C.c_double), en.shape[0], _ptr(en, C.c_int32),
+                     fe.shape[0], _ptr(fe, C.c_int32), _ptr(fl, C.c_int8), _ptr(fc, C.c_int8),
+                     dd.shape[0], _ptr(dd, C.c_int64), _ptr(dv, C.c_double),
+                     nf_.shape[0], _ptr(nf_, C.c_int32), _ptr(nt, C.c_double))
+    return d, keep
+
+
+def desc_of(m):
+    """make_desc for an object with the mesh attributes (dim, xyz, elem_nodes,
+    face_elems, face_local, face_crackable, dir_dof, dir_val)."""
+    return make_desc(m.dim, m.xyz, m.elem_nodes, m.face_elems, m.face_local, m.face_crackable, m.dir_dof,
+                     m.dir_val)
+
+
+def hf_mesh_sizes(m):
+    d, keep = desc_of(m)
+    nu, np_ = C.c_int64(), C.c_int64()
+    st = load().hf_mesh_sizes(C.byref(d), C.byref(nu), C.byref(np_))
+    if st != HF_OK:
+        raise HFError(st, "hf_mesh_sizes")
+    return nu.value, np_.value
+
+
+def hf_estimate_device_bytes(m, jacobi_block=32):
+    d, keep = desc_of(m)
+    b = C.c_int64()
+    st = load().hf_estimate_device_bytes(C.byref(d), int(jacobi_block), C.byref(b))
+    if st != HF_OK:
+        raise HFError(st, "hf_estimate_device_bytes")
+    return b.value
+
+
+def solver_opts(**kw):
+    o = hf_solver_opts()
+    load().hf_default_solver_opts(C.byref(o))
+    for k, v in kw.items():
+        if k == "precision" and isinstance(v, str):
+            v = HF_PREC_MIXED if v == "mixed" else HF_PREC_FP64
+        setattr(o, k, v)
+    return o
+
+
+def step_opts(**kw):
+    o = hf_step_opts()
+    load().hf_default_step_opts(C.byref(o))
+    for k, v in kw.items():
+        setattr(o, k, v)
+    return o
+
+
 class HFMesh:
     """One discretised problem on the GPU (an hf_mesh handle)."""
 
     def __init__(self, dim, xyz, elem_nodes, face_elems, face_local, face_crackable, dir_dof, dir_val,
                  neu_face=None, neu_traction=None, stream=None):
         self.lib = load()
-        self._keep = [np.ascontiguousarray(xyz, dtype=np.float64),
-                      np.ascontiguousarray(elem_nodes, dtype=np.int32),
-                      np.ascontiguousarray(face_elems, dtype=np.int32),
-                      np.ascontiguousarray(face_local, dtype=np.int8),
-                      np.ascontiguousarray(face_crackable, dtype=np.int8),
-                      np.ascontiguousarray(dir_dof, dtype=np.int64),
-                      np.ascontiguousarray(dir_val, dtype=np.float64),
-                      np.ascontiguousarray(neu_face if neu_face is not None else np.zeros(0), dtype=np.int32),
-                      np.ascontiguousarray(neu_traction if neu_traction is not None else np.zeros(0),
-                                           dtype=np.float64)]
-        x, en, fe, fl, fc, dd, dv, nf_, nt = self._keep
-        d = hf_mesh_desc(dim, 2, x.shape[0], _ptr(x, C.c_double), en.shape[0], _ptr(en, C.c_int32),
-                         fe.shape[0], _ptr(fe, C.c_int32), _ptr(fl, C.c_int8), _ptr(fc, C.c_int8),
-                         dd.shape[0], _ptr(dd, C.c_int64), _ptr(dv, C.c_double),
-                         nf_.shape[0], _ptr(nf_, C.c_int32), _ptr(nt, C.c_double))
+        d, self._keep = make_desc(dim, xyz, elem_nodes, face_elems, face_local, face_crackable, dir_dof, dir_val,
+                                  neu_face, neu_traction)
+        fe = self._keep[2]
         h = C.c_void_p()
         st = self.lib.hf_mesh_create(C.byref(d), C.c_void_p(stream) if stream else None, C.byref(h))
         if st != HF_OK:
@@ -179,13 +281,17 @@ class HFMesh:
         return o
 
     def hf_set_solver(self, **kw):
-        o = self.default_opts()
-        for k, v in kw.items():
-            if k == "precision" and isinstance(v, str):
-                v = HF_PREC_MIXED if v == "mixed" else HF_PREC_FP64
-            setattr(o, k, v)
+        o = solver_opts(**kw)
         self._check(self.lib.hf_set_solver(self.h, C.byref(o)))
         return o
+
+    def hf_advance_step(self, **kw):
+        """One time step (Newton, criterion, end of step, cutbacks); returns the
+        step report as a dict."""
+        o = step_opts(**kw)
+        r = hf_step_report()
+        self._check(self.lib.hf_advance_step(self.h, C.byref(o), C.byref(r)))
+        return r.as_dict()
 
     def hf_set_state(self, U, P, alpha, beta, w_old=None, t=0.0):
         U = np.ascontiguousarray(U, dtype=np.float64)
@@ -268,7 +374,7 @@ class HFMesh:
         st = np.zeros(16, np.int64)
         self._check(self.lib.hf_get_stats(self.h, _ptr(st, C.c_int64)))
         keys = ["elements", "interior_slots", "subdomain_slots", "levels_max", "subdomains", "nl_faces",
-                "n_p", "faces", "kernel_launches", "graph_timing_error"]
+                "n_p", "faces", "kernel_launches", "graph_timing_error", "device_bytes"]
         return dict(zip(keys, (int(x) for x in st)))
 
     def hf_solve_linear(self, rhs):
@@ -277,3 +383,82 @@ class HFMesh:
         r = hf_newton_report()
         self._check(self.lib.hf_solve_linear(self.h, _ptr(rhs, C.c_double), _ptr(d, C.c_double), C.byref(r)))
         return d, r.as_dict()
+
+
+class HFRuntime:
+    """The request loop of include/hf.h (hf_runtime_*): admission by free slot
+    and device-memory budget, requests overlapping on the GPU."""
+
+    def __init__(self, slots=8, hbm_budget_bytes=200 << 30, max_bypass=8, device=0):
+        self.lib = load()
+        o = hf_runtime_opts(int(slots), int(hbm_budget_bytes), int(max_bypass), int(device))
+        h = C.c_void_p()
+        st = self.lib.hf_runtime_create(C.byref(o), C.byref(h))
+        if st != HF_OK:
+            raise HFError(st, "hf_runtime_create")
+        self.h = h
+
+    def submit(self, mesh, *, E, nu, sigma_c, delta_c, mu, Q0, inj_dofs, inj_weights, delta_f, dt, n_steps,
+               b_stab=10.0, p_vapor=0.0, cutoff_on=True, L_ref=1.0, solver=None, step=None, U0=None, P0=None,
+               alpha0=None, beta0=None, t0=0.0):
+        """Queue one request (mesh: an object with the mesh attributes); the
+        runtime copies every array before this returns.  Returns its id."""
+        d, keep = desc_of(mesh)
+        inj = np.ascontiguousarray(inj_dofs, dtype=np.int64)
+        wts = np.ascontiguousarray(inj_weights, dtype=np.float64)
+        arrs = [None if a is None else np.ascontiguousarray(a, dtype=t)
+                for a, t in ((U0, np.float64), (P0, np.float64), (alpha0, np.int8), (beta0, np.int8))]
+        r = hf_request(C.pointer(d), E, nu, sigma_c, delta_c, b_stab, mu, Q0, inj.shape[0], _ptr(inj, C.c_int64),
+                       _ptr(wts, C.c_double), delta_f, dt, p_vapor, int(bool(cutoff_on)), L_ref,
+                       solver_opts(**(solver or {})), step_opts(**(step or {})), int(n_steps),
+                       _ptr(arrs[0], C.c_double), _ptr(arrs[1], C.c_double), _ptr(arrs[2], C.c_int8),
+                       _ptr(arrs[3], C.c_int8), float(t0))
+        i = C.c_int64()
+        st = self.lib.hf_runtime_submit(self.h, C.byref(r), C.byref(i))
+        if st != HF_OK:
+            raise HFError(st, "hf_runtime_submit")
+        return i.value
+
+    def wait(self, rid, timeout=-1.0):
+        """The request's hf_result as a dict, or None if it has not finished
+        within timeout seconds."""
+        res = hf_result()
+        st = self.lib.hf_runtime_wait(self.h, int(rid), float(timeout), C.byref(res))
+        if st == -6:
+            return None
+        if st != HF_OK:
+            raise HFError(st, "hf_runtime_wait")
+        return res.as_dict()
+
+    def fetch(self, rid, res):
+        """Final state (U, P, alpha, beta) of a finished request; forgets it."""
+        U = np.zeros(max(res["n_u"], 1))
+        P = np.zeros(max(res["n_p"], 1))
+        a = np.zeros(max(res["n_faces"], 1), np.int8)
+        b = np.zeros(max(res["n_faces"], 1), np.int8)
+        st = self.lib.hf_runtime_fetch(self.h, int(rid), _ptr(U, C.c_double), _ptr(P, C.c_double), _ptr(a, C.c_int8),
+                                       _ptr(b, C.c_int8))
+        if st != HF_OK:
+            raise HFError(st, "hf_runtime_fetch")
+        return U[: res["n_u"]], P[: res["n_p"]], a[: res["n_faces"]], b[: res["n_faces"]]
+
+    def stats(self):
+        st = np.zeros(8, np.int64)
+        self.lib.hf_runtime_stats(self.h, _ptr(st, C.c_int64))
+        keys = ["queued", "running", "unfetched", "admitted_bytes", "peak_bytes", "peak_running", "completed",
+                "failed"]
+        return dict(zip(keys, (int(x) for x in st)))
+
+    def now(self):
+        return float(self.lib.hf_runtime_now(self.h))
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hf_runtime_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhfgb300.so")
-SOURCES = ["hf_api.cu", "hf_assembly.cu", "hf_solve.cu", "hf_noalloc.cu"]
+SOURCES = ["hf_api.cu", "hf_assembly.cu", "hf_solve.cu", "hf_noalloc.cu", "hf_runtime.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
 
@@ -55,7 +55,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp"
-        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart"])
+        run([cc, *ARCH, "-shared", "-o", tmp, *objs, "-lcudart", "-lpthread"])
         os.replace(tmp, LIB)
     return LIB
 

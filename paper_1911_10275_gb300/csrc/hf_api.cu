@@ -4,6 +4,7 @@
 // schedule, quadrature nodes) and sequences kernels; every term of the
 // residual, the Jacobian and the solve is computed on the GPU.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <cstring>
@@ -17,9 +18,12 @@ using namespace hfk;
 
 namespace hfk {
 long long& launch_counter() {
-  static long long n = 0;
+  thread_local long long n = 0;
   return n;
 }
+static std::atomic<long long> g_launches{0};
+void add_launches(long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+long long total_launches() { return g_launches.load(std::memory_order_relaxed); }
 }  // namespace hfk
 
 namespace hfk {
@@ -167,19 +171,43 @@ static void build_quad(int dim, Quad& q) {
 }
 
 // ---------------------------------------------------------------- helpers
+namespace hfk {
+void* dev_alloc(hf_mesh* h, size_t bytes) {
+  bytes = (std::max<size_t>(bytes, 1) + 255) / 256 * 256;
+  void* raw = nullptr;
+  if (cudaMallocAsync(&raw, bytes + 256, h->stream) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  void* base = reinterpret_cast<void*>((reinterpret_cast<uintptr_t>(raw) + 255) & ~uintptr_t(255));
+  h->allocs.push_back({raw, base, bytes});
+  h->bytes_allocated += (long long)bytes;
+  return base;
+}
+
+void dev_free(hf_mesh* h, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < h->allocs.size(); ++i)
+    if (h->allocs[i].base == p) {
+      cudaFreeAsync(h->allocs[i].raw, h->stream);
+      h->bytes_allocated -= (long long)h->allocs[i].bytes;
+      h->allocs[i] = h->allocs.back();
+      h->allocs.pop_back();
+      return;
+    }
+}
+}  // namespace hfk
+
 template <typename T> static T* upload(hf_mesh* h, const std::vector<T>& v) {
-  void* p = nullptr;
-  size_t n = std::max<size_t>(v.size(), 1);
-  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
-  h->allocs.push_back(p);
+  void* p = dev_alloc(h, std::max<size_t>(v.size(), 1) * sizeof(T));
+  if (!p) return nullptr;
   if (!v.empty()) cudaMemcpyAsync(p, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice, h->stream);
   return reinterpret_cast<T*>(p);
 }
 template <typename T> static T* dzeros(hf_mesh* h, size_t n) {
-  void* p = nullptr;
   n = std::max<size_t>(n, 1);
-  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
-  h->allocs.push_back(p);
+  void* p = dev_alloc(h, n * sizeof(T));
+  if (!p) return nullptr;
   cudaMemsetAsync(p, 0, n * sizeof(T), h->stream);
   return reinterpret_cast<T*>(p);
 }
@@ -251,6 +279,7 @@ static hf_status rebuild_lists(hf_mesh* h) {
     if (sd_coh[s]) h->sd_always.push_back(s);
   if (h->nl_cap < (int)nl.size() || !h->d.nl_faces) {
     h->nl_cap = std::max<int>((int)nl.size(), 64);
+    dev_free(h, h->d.nl_faces);
     h->d.nl_faces = dzeros<int>(h, h->nl_cap);
     if (!h->d.nl_faces) return set_error(h, HF_ERR_OOM, "nonlinear facet list");
   }
@@ -305,6 +334,8 @@ static hf_status build_subdomains(hf_mesh* h, int G) {
   h->G = G;
   h->d.G = G;
   h->d.nsd = nsd;
+  for (void* old : {(void*)h->d.sd_elems, (void*)h->d.sd_lvl, (void*)h->d.sd_lvl_base, (void*)h->d.sd_nlvl})
+    dev_free(h, old);
   h->d.sd_elems = upload(h, sd_elems);
   h->d.sd_lvl = upload(h, sd_lvl);
   h->d.sd_lvl_base = upload(h, sd_base);
@@ -361,6 +392,9 @@ static hf_status build_subdomains(hf_mesh* h, int G) {
     sd_fwd[s] = c ? rec_fwd[sd_elems[b]] : 0;
     sd_bwd[s] = c ? rec_bwd[sd_elems[b + c - 1]] : 0;
   }
+  for (void* old : {(void*)h->d.rec_fwd, (void*)h->d.rec_bwd, (void*)h->d.sd_task, (void*)h->d.sd_fwd,
+                    (void*)h->d.sd_bwd})
+    dev_free(h, old);
   h->d.rec_fwd = upload(h, rec_fwd);
   h->d.rec_bwd = upload(h, rec_bwd);
   h->d.sd_task = upload(h, task);
@@ -458,7 +492,8 @@ hf_status hf_mesh_destroy(hf_mesh* h) {
   invalidate_graphs(h);
   for (int i = 0; i < 2 * PROF_EVENTS; ++i)
     if (h->prof.ev[i]) cudaEventDestroy(h->prof.ev[i]);
-  for (void* p : h->allocs) cudaFree(p);
+  for (const hf_mesh::Alloc& a : h->allocs) cudaFreeAsync(a.raw, h->stream);
+  if (h->stream) cudaStreamSynchronize(h->stream);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return HF_OK;
@@ -939,6 +974,60 @@ hf_status hf_accept_step(hf_mesh* h, int64_t* n_new_beta) {
   return check_cuda(h, cudaStreamSynchronize(h->stream), "accept");
 }
 
+// ---------------------------------------------------------------- time step
+// Start-of-step state kept on the device, so a failed attempt is undone
+// without a host round trip.
+static hf_status snap_save(hf_mesh* h) {
+  if (!h->snap_X) {
+    h->snap_X = static_cast<double*>(dev_alloc(h, h->N * sizeof(double)));
+    h->snap_wold = static_cast<double*>(dev_alloc(h, (size_t)h->nfn * h->nf * sizeof(double)));
+    if (!h->snap_X || !h->snap_wold) return set_error(h, HF_ERR_OOM, "step snapshot");
+  }
+  HF_CUDA(h, cudaMemcpyAsync(h->snap_X, h->X, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  HF_CUDA(h, cudaMemcpyAsync(h->snap_wold, h->d.w_old, (size_t)h->nfn * h->nf * sizeof(double),
+                             cudaMemcpyDeviceToDevice, h->stream));
+  h->snap_alpha = h->h_alpha;
+  h->snap_beta = h->h_beta;
+  h->snap_t = h->t;
+  return HF_OK;
+}
+
+static hf_status snap_restore(hf_mesh* h) {
+  HF_CUDA(h, cudaMemcpyAsync(h->X, h->snap_X, h->N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  HF_CUDA(h, cudaMemcpyAsync(h->d.w_old, h->snap_wold, (size_t)h->nfn * h->nf * sizeof(double),
+                             cudaMemcpyDeviceToDevice, h->stream));
+  std::vector<int> changed;
+  for (long long f = 0; f < h->nf; ++f)
+    if (h->h_alpha[f] != h->snap_alpha[f]) {
+      changed.push_back(h->h_fe[f]);
+      if (h->h_fe[h->nf + f] >= 0) changed.push_back(h->h_fe[h->nf + f]);
+    }
+  h->h_alpha = h->snap_alpha;
+  h->h_beta = h->snap_beta;
+  h->t = h->snap_t;
+  hf_status s = rebuild_lists(h);
+  if (s) return s;
+  std::sort(changed.begin(), changed.end());
+  changed.erase(std::unique(changed.begin(), changed.end()), changed.end());
+  if ((s = rebuild_rows(h, changed))) return s;
+  launch_fluid_scale(h->d, h->opts.fluid_scaling, h->L_ref, h->stream);
+  return check_cuda(h, cudaGetLastError(), "restore");
+}
+
+// the time-step length enters the facet records and the pressure rows, both
+// baked into captured GMRES cycles
+static void set_dt(hf_mesh* h, double dt) {
+  if (dt == h->dt) return;
+  h->dt = dt;
+  h->d.dt = dt;
+  invalidate_graphs(h);
+}
+
+static bool fatal(hf_mesh* h, hf_status s) {
+  return h->poisoned || s == HF_ERR_CUDA || s == HF_ERR_TIMEOUT || s == HF_ERR_DEVICE_ASSERT || s == HF_ERR_OOM ||
+         s == HF_ERR_INVALID_ARG || s == HF_ERR_STATE;
+}
+
 hf_status hf_get_opening_pressure(hf_mesh* h, double* w_face_nodes, double* p, int8_t* alpha, int8_t* beta) {
   HF_GUARD(h);
   if (w_face_nodes) {
@@ -1062,9 +1151,168 @@ hf_status hf_get_stats(const hf_mesh* h, int64_t* st) {
   st[5] = h->d.n_nl;
   st[6] = h->np;
   st[7] = h->nf;
-  st[8] = launch_counter();
+  st[8] = total_launches();
   st[9] = h->prof.graph_timing_error;
-  for (int i = 10; i < 16; ++i) st[i] = 0;
+  st[10] = h->bytes_allocated;
+  for (int i = 11; i < 16; ++i) st[i] = 0;
+  return HF_OK;
+}
+
+void hf_default_step_opts(hf_step_opts* o) {
+  if (!o) return;
+  o->newton_max = 8;
+  o->criterion_rounds = 4;
+  o->max_cutbacks = 10;
+}
+
+hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* rep) {
+  HF_GUARD(h);
+  if (!h->material_set || !h->injection_set) return set_error(h, HF_ERR_STATE, "set material and injection first");
+  hf_step_opts o;
+  hf_default_step_opts(&o);
+  if (opts) o = *opts;
+  if (o.newton_max < 1 || o.criterion_rounds < 1 || o.max_cutbacks < 0)
+    return set_error(h, HF_ERR_INVALID_ARG, "step options out of range");
+  hf_step_report r{};
+  const double dt0 = h->dt, target = h->t + dt0;
+  double sub = dt0;
+  int cuts = 0;
+  hf_status s = snap_save(h);
+  if (s) return s;
+  while (target - h->t > 1e-12 * dt0) {
+    sub = std::min(sub, target - h->t);
+    set_dt(h, sub);
+    bool ok = false;
+    int rounds = 0, it = 0;
+    for (;;) {  // Newton to convergence, then the criterion; Newton again if it switched facets
+      hf_newton_report nr{};
+      s = hf_newton_step(h, &nr);
+      if (s != HF_OK) {
+        if (fatal(h, s)) {
+          set_dt(h, dt0);
+          return s;
+        }
+        break;
+      }
+      ++r.newton_iters;
+      r.gmres_iters += nr.gmres_iters;
+      r.du_rel = nr.du_rel;
+      r.dp_rel = nr.dp_rel;
+      ++it;
+      if (!nr.lin_converged) break;
+      if (nr.converged) {
+        int64_t na = 0;
+        if ((s = hf_check_fracture_criterion(h, &na))) {
+          set_dt(h, dt0);
+          return s;
+        }
+        r.new_alpha += na;
+        if (na == 0 || ++rounds >= o.criterion_rounds) {
+          ok = true;
+          break;
+        }
+        it = 0;
+        continue;
+      }
+      if (it >= o.newton_max) break;
+    }
+    if (ok) {
+      int64_t nb = 0;
+      if ((s = hf_accept_step(h, &nb))) {
+        set_dt(h, dt0);
+        return s;
+      }
+      r.new_beta += nb;
+      ++r.substeps;
+      if ((s = snap_save(h))) return s;
+      sub = std::min(dt0, 1.5 * sub);
+    } else {
+      if ((s = snap_restore(h))) return s;
+      if (++cuts > o.max_cutbacks) {
+        set_dt(h, dt0);
+        if (rep) *rep = r;
+        return set_error(h, HF_ERR_NOT_CONVERGED, "time step not converged after the allowed cutbacks");
+      }
+      ++r.cutbacks;
+      sub *= 0.5;
+    }
+  }
+  h->t = target;
+  set_dt(h, dt0);
+  r.t = h->t;
+  if (rep) *rep = r;
+  return check_cuda(h, cudaStreamSynchronize(h->stream), "advance_step");
+}
+
+// pressure unknowns (distinct nodes of crackable interior facets) and the
+// number of crackable interior facets, from the descriptor alone
+static hf_status desc_counts(const hf_mesh_desc* desc, long long* np_out, long long* ncrack_out) {
+  if (!desc || (desc->dim != 2 && desc->dim != 3) || desc->n_elems <= 0 || desc->n_faces <= 0 ||
+      desc->n_nodes <= 0 || !desc->elem_nodes || !desc->face_elems || !desc->face_local || !desc->face_crackable)
+    return HF_ERR_INVALID_ARG;
+  const long long dim = desc->dim, ne = desc->n_elems, nf = desc->n_faces, nn = desc->n_nodes;
+  const long long nen = dim == 2 ? 6 : 10, nfn = dim == 2 ? 3 : 6;
+  std::vector<char> mark(nn, 0);
+  long long ncrack = 0;
+  for (long long f = 0; f < nf; ++f) {
+    int em = desc->face_elems[2 * f], ep = desc->face_elems[2 * f + 1], jm = desc->face_local[2 * f];
+    if (ep < 0 || !desc->face_crackable[f] || em < 0 || em >= ne || jm < 0 || jm > dim) continue;
+    ++ncrack;
+    for (int a = 0; a < nfn; ++a) {
+      int g = desc->elem_nodes[(long long)em * nen + fnode((int)dim, jm, a)];
+      if (g >= 0 && g < nn) mark[g] = 1;
+    }
+  }
+  long long np = 0;
+  for (long long g = 0; g < nn; ++g) np += mark[g];
+  *np_out = np;
+  *ncrack_out = ncrack;
+  return HF_OK;
+}
+
+hf_status hf_mesh_sizes(const hf_mesh_desc* desc, int64_t* n_u, int64_t* n_p) {
+  long long np = 0, ncrack = 0;
+  hf_status s = desc_counts(desc, &np, &ncrack);
+  if (s) return s;
+  if (n_u) *n_u = desc->n_elems * (desc->dim == 2 ? 12 : 30);
+  if (n_p) *n_p = np;
+  return HF_OK;
+}
+
+hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, int jacobi_block, int64_t* bytes) {
+  long long np = 0, ncrack = 0;
+  if (!bytes || desc_counts(desc, &np, &ncrack) != HF_OK) return HF_ERR_INVALID_ARG;
+  const long long dim = desc->dim, ne = desc->n_elems, nf = desc->n_faces, nn = desc->n_nodes;
+  const long long nen = dim == 2 ? 6 : 10, ned = nen * dim, nfn = dim == 2 ? 3 : 6, nfr = nfn * dim, nsl = dim + 1;
+  const long long nld = 4 * nfn * nfn + 3 * nfn, lus = ned * ned + nsl * ned * nfr;
+  const long long nu = ne * ned, N = nu + np;
+  const long long G = std::max(1, std::min(jacobi_block, 256)), nsd = (ne + G - 1) / G;
+  const long long nmat = ne * (ned * ned + nsl * ned * nfr), ldv = (N + 63) / 64 * 64;
+  long long t = 0;
+  auto add = [&](long long b) { t += (std::max(b, 1LL) + 255) / 256 * 256; };
+  // mesh arrays
+  add(nn * dim * 8); add(nen * ne * 4); add((dim + 1) * dim * ne * 8); add(ne * 8);
+  add(nsl * ne * 4); add(nsl * ne * 4); add(nsl * ne); add(ne * 4); add(ne);
+  add(2 * nf * 4); add(2 * nf); add(dim * nf * 8); add(nf * 8); add(nf * 8); add(dim * dim * nf * 8);
+  add(nfn * nf); add(nfn * nf); add(nfn * nf * 4); add(nf); add(nf); add(nf); add(nfn * nf * 8);
+  add(nf * nld * 8); add((np + 1) * 4); add(ncrack * nfn * 4); add(ncrack * nfn); add(np); add(np * 8);
+  add(nu * 8); add(nu * 8); add(16 * 8); add(4 * 4); add(dim * nf * 8); add(nf);
+  add(nmat * 8);
+  for (int i = 0; i < 5; ++i) add(N * 8);
+  add(ne * 4); add(16 * 4); add(16 * 8); add(nfn * nf * 8);
+  // subdomains, level schedule, record streams, task table, nonlinear list
+  add(ne * 4); add((ne + nsd) * 4); add(nsd * 4); add(nsd * 4);  // levels per subdomain <= its elements
+  add(ne); add(ne); add(ne * 4);
+  add(ne * 8); add(ne * 8); add(ne * 8); add(nsd * 8); add(nsd * 8);
+  add(std::max(ncrack, 64LL) * 4);
+  // solver workspace of both precisions
+  add(ldv * 31 * 8); for (int i = 0; i < 5; ++i) add(N * 8);
+  add(ldv * 31 * 4); for (int i = 0; i < 5; ++i) add(N * 4);
+  add(ne * lus * 8); add(ne * lus * 4); add(std::max(np, 1LL) * 8); add(std::max(np, 1LL) * 4);
+  add(nmat * 4); add(152 * 4 * 32 * 8); add((long long)sizeof(GmresState));
+  // time-step snapshot
+  add(N * 8); add(nfn * nf * 8);
+  *bytes = t;
   return HF_OK;
 }
 

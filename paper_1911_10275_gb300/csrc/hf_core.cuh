@@ -25,8 +25,13 @@
 namespace hfk {
 
 // process-wide count of kernel launches issued by the library (host side)
-long long& launch_counter();
-inline void note_launch() { ++launch_counter(); }
+long long& launch_counter();        // kernels launched by the calling host thread
+void add_launches(long long n);     // process-wide total, shared by all threads
+long long total_launches();
+inline void note_launch() {
+  ++launch_counter();
+  add_launches(1);
+}
 
 constexpr int MAXFN = 6;     // face nodes of a P2 facet (3D)
 constexpr int MAXNED = 30;   // unknowns of a P2 tetrahedron

@@ -115,7 +115,13 @@ struct hf_mesh {
   // device buffers
   hfk::DevMesh d{};
   hfk::Quad q{};
-  std::vector<void*> allocs;
+  struct Alloc {
+    void* raw;      // pointer returned by the stream-ordered allocator
+    void* base;     // 256-byte aligned start handed out
+    size_t bytes;
+  };
+  std::vector<Alloc> allocs;
+  long long bytes_allocated = 0;
   hfk::EBMat<double> J64;
   hfk::EBMat<float> J32;
   bool j32_valid = false;
@@ -151,9 +157,20 @@ struct hf_mesh {
   long long graph_kernels64 = 0, graph_kernels32 = 0;  // kernel nodes per captured cycle
   hfk::Prof prof;
   long long n_interior_slots = 0, n_subdomain_slots = 0;
+
+  // start-of-step snapshot of hf_advance_step (restored when a step is cut)
+  double* snap_X = nullptr;
+  double* snap_wold = nullptr;
+  std::vector<signed char> snap_alpha, snap_beta;
+  double snap_t = 0.0;
 };
 
 namespace hfk {
+// device memory of a handle: stream-ordered on its stream (no device-wide
+// synchronisation, so handles on other streams keep running), 256-byte
+// aligned, released by dev_free or at hf_mesh_destroy
+void* dev_alloc(hf_mesh* h, size_t bytes);
+void dev_free(hf_mesh* h, void* p);
 // solver side (hf_solve.cu)
 hf_status solver_alloc(hf_mesh* h);
 void convert_j32(hf_mesh* h);

@@ -18,6 +18,8 @@
 //    see the done flag and return at once.
 //  * Mixed precision: FP32 matrix, factor and Krylov vectors inside FP64
 //    iterative refinement (residual and update in FP64).
+#include <atomic>
+#include <mutex>
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -1184,10 +1186,7 @@ static int grid_for(long long n, int threads, int cap) {
 }
 
 template <typename T> static T* dalloc(hf_mesh* h, size_t n) {
-  void* p = nullptr;
-  if (cudaMalloc(&p, n * sizeof(T)) != cudaSuccess) return nullptr;
-  h->allocs.push_back(p);
-  return reinterpret_cast<T*>(p);
+  return reinterpret_cast<T*>(dev_alloc(h, n * sizeof(T)));
 }
 
 hf_status solver_alloc(hf_mesh* h) {
@@ -1286,10 +1285,16 @@ template <int DIM, typename T> static size_t apply_smem(int G, int W) {
 template <typename T, int DIM, int W>
 static void launch_apply(hf_mesh* h, const T* lu, const T* rin, T* z, const int* skip) {
   size_t sm = apply_smem<DIM, T>(h->G, W);
-  static size_t configured = 0;
-  if (sm > 48 * 1024 && sm > configured) {
-    cudaFuncSetAttribute(k_ilu_apply<T, DIM, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    configured = sm;
+  // the opt-in limit only grows, so that handles driven from several host
+  // threads never lower it under one another
+  static std::atomic<size_t> configured{0};
+  static std::mutex raise;
+  if (sm > 48 * 1024 && sm > configured.load()) {
+    std::lock_guard<std::mutex> lock(raise);
+    if (sm > configured.load()) {
+      cudaFuncSetAttribute(k_ilu_apply<T, DIM, W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+      configured.store(sm);
+    }
   }
   { note_launch(); k_ilu_apply<T, DIM, W><<<(h->d.nsd + W - 1) / W, 32 * W, sm, h->stream>>>(h->d, lu, rin, z, skip); }
 }
@@ -1360,6 +1365,7 @@ static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, 
     gmres_cycle<T, DIM>(h, K, dg, off, mrest);
     gk = launch_counter() - before;  // kernel nodes of the graph, counted per replay
     launch_counter() = before;
+    add_launches(-gk);
     h->prof.capturing = false;
     h->prof.cap_list = nullptr;
     e = cudaStreamEndCapture(h->stream, &g);
@@ -1369,6 +1375,7 @@ static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, 
     if (e != cudaSuccess) return check_cuda(h, e, "cudaGraphInstantiate");
   }
   launch_counter() += gk;
+  add_launches(gk);
   return check_cuda(h, cudaGraphLaunch(*gexec, h->stream), "cudaGraphLaunch");
 }
 

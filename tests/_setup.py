@@ -49,3 +49,54 @@ def with_extra_cohesive(wl, state, count=1, opening=3e-5):
 def rel_err(a, b):
     scale = np.abs(b).max()
     return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
+
+
+def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
+    """One time step of Sec. 3 on the oracle, with the driver rules of
+    hf_advance_step: Newton until converged, the criterion, Newton again if it
+    switched facets (at most rounds_max rounds), end of step; an attempt that
+    does not converge within newton_max iterations (or turns non-finite) is
+    undone and retried with half the sub-step, which grows back by 1.5 after
+    each accepted sub-step until t + dt is reached."""
+    dt0 = o.prm.dt
+    target = o.t + dt0
+    sub = dt0
+    rep = {"newton_iters": 0, "cutbacks": 0, "substeps": 0}
+
+    def snap():
+        return (o.U.copy(), o.P.copy(), o.alpha.copy(), o.beta.copy(), o.w_old.copy(), o.t)
+
+    saved = snap()
+    while target - o.t > 1e-12 * dt0:
+        sub = min(sub, target - o.t)
+        o.prm.dt = sub
+        ok, rounds, it = False, 0, 0
+        while True:
+            r = o.newton_step()
+            rep["newton_iters"] += 1
+            it += 1
+            if not (np.isfinite(r["du_rel"]) and np.isfinite(r["dp_rel"])):
+                break
+            if r["converged"]:
+                n_new, _ = o.check_fracture_criterion()
+                rounds += 1
+                if n_new == 0 or rounds >= rounds_max:
+                    ok = True
+                    break
+                it = 0
+                continue
+            if it >= newton_max:
+                break
+        if ok:
+            o.accept_step()
+            rep["substeps"] += 1
+            saved = snap()
+            sub = min(dt0, 1.5 * sub)
+        else:
+            o.set_state(*saved)
+            rep["cutbacks"] += 1
+            assert rep["cutbacks"] <= max_cutbacks
+            sub *= 0.5
+    o.t = target
+    o.prm.dt = dt0
+    return rep

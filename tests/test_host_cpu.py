@@ -1,0 +1,122 @@
+"""Host-side logic without a GPU: unknown counts and the device-memory bound
+computed by the library from a descriptor, the replica split of independent
+instances (with a two-rank gloo group), the serving client's bookkeeping and
+the request generators."""
+import os
+import socket
+
+import numpy as np
+import pytest
+
+from hf_inputs import kgd_2d, penny_3d, sweep_instances, serving_requests
+from _setup import oracle_for
+
+
+@pytest.mark.parametrize("make", [lambda: kgd_2d(n=8), lambda: kgd_2d(n=6, crackable="all"),
+                                  lambda: penny_3d(n=4, crackable="plane"), lambda: penny_3d(n=2)])
+def test_mesh_sizes_match_the_oracle(make):
+    from paper_1911_10275_gb300 import hf_mesh_sizes
+    wl = make()
+    o = oracle_for(wl)
+    assert hf_mesh_sizes(wl.mesh) == (o.Nu, o.Np)
+
+
+def test_device_bound_grows_with_the_mesh_and_covers_the_matrices():
+    from paper_1911_10275_gb300 import hf_estimate_device_bytes
+    prev = 0
+    for n in (8, 16, 32):
+        m = kgd_2d(n=n).mesh
+        b = hf_estimate_device_bytes(m, 32)
+        ne = m.n_elems
+        # J in FP64 and FP32 plus both ILU record sets: 4 (12x12 + 3 * 12x6) values per element
+        assert b >= ne * (144 + 216) * (8 + 4) * 2
+        assert b > prev
+        prev = b
+    m = penny_3d(n=4).mesh
+    assert hf_estimate_device_bytes(m, 8) >= hf_estimate_device_bytes(m, 64)
+
+
+def test_partition_is_balanced_complete_and_deterministic():
+    from paper_1911_10275_gb300.replicas import partition
+    rng = np.random.default_rng(0)
+    costs = rng.lognormal(size=101)
+    for world in (1, 2, 3, 8):
+        parts = partition(costs, world)
+        flat = sorted(i for p in parts for i in p)
+        assert flat == list(range(101))
+        loads = [costs[p].sum() for p in parts]
+        # LPT bound: no rank exceeds the mean by more than the largest item
+        assert max(loads) <= np.mean(loads) + costs.max() + 1e-12
+        assert parts == partition(list(costs), world)
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _rank_main(rank, world, port, costs, q):
+    import torch.distributed as dist
+    from paper_1911_10275_gb300.replicas import my_share, max_over_ranks, sum_over_ranks
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    mine = my_share(costs, rank, world)
+    got = [None] * world
+    dist.all_gather_object(got, mine)
+    slowest = max_over_ranks(10.0 + rank)
+    total = sum_over_ranks(len(mine))
+    dist.destroy_process_group()
+    q.put((rank, got, slowest, total))
+
+
+def test_replicas_on_two_gloo_ranks():
+    """Each rank takes its own share of the instances with no exchange; the
+    shares agree across ranks, cover every instance once, and the job time is
+    the slowest rank's."""
+    import torch.multiprocessing as mp
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    costs = [float(c) for c in np.random.default_rng(1).uniform(1, 5, size=37)]
+    port = _free_port()
+    procs = [ctx.Process(target=_rank_main, args=(r, 2, port, costs, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    out.sort()
+    assert out[0][1] == out[1][1]
+    shares = out[0][1]
+    assert sorted(shares[0] + shares[1]) == list(range(37))
+    assert out[0][2] == out[1][2] == 11.0
+    assert out[0][3] == out[1][3] == 37.0
+
+
+def test_latency_summary_percentiles():
+    from paper_1911_10275_gb300.serving import latency_summary
+    recs = [{"status": 0, "latency": (i + 1) / 1000.0, "t_submit": 0.0, "t_done": (i + 1) / 1000.0,
+             "newton_iters": 3, "gmres_iters": 10, "cutbacks": 0} for i in range(100)]
+    recs.append({"status": -4, "latency": 9.0, "t_submit": 0.0, "t_done": 0.05, "newton_iters": 0,
+                 "gmres_iters": 0, "cutbacks": 10})
+    s = latency_summary(recs)
+    assert s["completed"] == 100 and s["failed"] == 1
+    assert abs(s["p50_ms"] - 50.5) < 1e-9 and abs(s["p99_ms"] - 99.01) < 1e-9
+    assert abs(s["throughput_req_s"] - 1000.0) < 1e-9
+
+
+def test_generators_are_seeded_and_in_range():
+    a = sweep_instances(16)
+    b = sweep_instances(16)
+    assert [w.name for w in a] == [w.name for w in b]
+    for w in a:
+        assert 1000 / 1.2 <= w.mesh.n_elems <= 50000 * 1.2
+        assert 5e9 <= w.E <= 50e9 and 0.1e6 <= w.K_Ic <= 3e6 and 1e-3 <= w.mu <= 1.0 and 1e-4 <= w.Q0 <= 1e-2
+    t, r = serving_requests(40, rate=200.0, kgd_n=(50, 60), penny_n=(7, 8))
+    assert np.all(np.diff(t) > 0) and abs(np.mean(np.diff(t)) - 1 / 200.0) < 2.5e-3
+    dims = {w.mesh.dim for w in r}
+    assert dims == {2, 3}
