@@ -416,6 +416,109 @@ def oracle_baseline(wl, budget_s):
                       f"(infeasible at this size), so an upper bound; set-up {t_setup:.1f} s"}
 
 
+def _solver_for_requests(args, tuner=None):
+    base = {"precision": args.precision, "rtol": 1e-8, "inner_rtol": 1e-3, "max_iters": 20000, "newton_tol": 1e-8,
+            "use_graphs": 1, "jacobi_block": args.jacobi_block, "restart": args.restart}
+    if tuner is None:
+        return lambda wl: dict(base)
+    return lambda wl: {**tuner.solver_for(wl, args.precision), "max_iters": 20000}
+
+
+def serving_run(args, count, rate, slots, seed=191110275, warm=True):
+    """Poisson stream of KGD and penny requests through the native request
+    loop; returns the latency summary and the run's description."""
+    import torch
+    from hf_inputs import serving_requests
+    from paper_1911_10275_gb300 import HFRuntime
+    from paper_1911_10275_gb300.serving import run_stream, latency_summary
+    cache = {}
+    t_gen = time.perf_counter()
+    arrivals, reqs = serving_requests(count, rate=rate, seed=seed, steps=args.serve_steps, mesh_cache=cache)
+    t_gen = time.perf_counter() - t_gen
+    free, total = torch.cuda.mem_get_info()
+    budget = int(0.8 * free)
+    rt = HFRuntime(slots=slots, hbm_budget_bytes=budget)
+    solver_for = _solver_for_requests(args)
+    if warm:  # one small request first, so that module loading is not in the first latency
+        run_stream(rt, [0.0], reqs[:1], 1, solver_for)
+    recs = run_stream(rt, arrivals, reqs, args.serve_steps, solver_for)
+    st = rt.stats()
+    rt.close()
+    summ = latency_summary(recs)
+    summ.update({"requests": count, "rate_req_s": rate, "slots": slots, "steps_per_request": args.serve_steps,
+                 "hbm_budget_gb": round(budget / 1e9, 1), "peak_admitted_gb": round(st["peak_bytes"] / 1e9, 2),
+                 "peak_running": st["peak_running"], "precision": args.precision,
+                 "unknowns_range": [int(min(r["n_u"] + r["n_p"] for r in recs)),
+                                    int(max(r["n_u"] + r["n_p"] for r in recs))],
+                 "kinds": {"kgd2d": sum(1 for w in reqs if w.mesh.dim == 2),
+                           "penny3d": sum(1 for w in reqs if w.mesh.dim == 3)},
+                 "mesh_generation_s": round(t_gen, 1)})
+    return summ, recs
+
+
+def run_serve(args):
+    """The serving configuration: a Poisson stream of solve requests (half
+    2D KGD, half 3D penny), admitted by HBM budget into `slots` concurrent
+    requests; p50/p99 latency and throughput."""
+    import torch
+    torch.cuda.set_device(0)
+    sampler = ClockSampler(0)
+    sampler.start()
+    summ, recs = serving_run(args, args.serve_requests, args.serve_rate, args.slots)
+    clocks = sampler.stop()
+    out = {"metric": "serving latency p99 (ms) under a Poisson request stream", "value": summ.get("p99_ms"),
+           "unit": "ms", "n_gpus": 1, "higher_is_better": False, "mode": "serve", "data": "synthetic",
+           "dtype": "f32-inner/f64-refinement" if args.precision == "mixed" else "f64",
+           "config": {"workload": "serving stream: KGD n in [50, 316] and penny n in [8, 22], 5 steps each"},
+           "serving": summ, "clocks": clocks}
+    print(json.dumps(out))
+
+
+def run_sweep(args):
+    """The batched sweep: independent 2D KGD instances of uneven size, all
+    submitted at once to the request loop, solver shape per size class from
+    the autotuner; aggregate Newton iterations per second and makespan."""
+    import torch
+    from hf_inputs import sweep_instances
+    from paper_1911_10275_gb300 import HFRuntime
+    from paper_1911_10275_gb300.autotune import Tuner
+    from paper_1911_10275_gb300.serving import run_stream, latency_summary
+    torch.cuda.set_device(0)
+    cache = {}
+    wls = sweep_instances(args.sweep_count, mesh_cache=cache, steps=args.sweep_steps)
+    tuner = None
+    t_tune = 0.0
+    if args.autotune:
+        tuner = Tuner()
+        t0 = time.perf_counter()
+        for wl in wls:
+            tuner.tune(wl, args.precision)
+        t_tune = time.perf_counter() - t0
+    free, _ = torch.cuda.mem_get_info()
+    rt = HFRuntime(slots=args.slots, hbm_budget_bytes=int(0.8 * free))
+    solver_for = _solver_for_requests(args, tuner)
+    sampler = ClockSampler(0)
+    sampler.start()
+    t0 = time.perf_counter()
+    recs = run_stream(rt, [0.0] * len(wls), wls, args.sweep_steps, solver_for)
+    span = time.perf_counter() - t0
+    clocks = sampler.stop()
+    st = rt.stats()
+    rt.close()
+    summ = latency_summary(recs)
+    newton = sum(r["newton_iters"] for r in recs if r["status"] == 0)
+    out = {"metric": "batched sweep: aggregate Newton iterations per second", "value": newton / span,
+           "unit": "Newton it/s", "n_gpus": 1, "higher_is_better": True, "mode": "sweep", "data": "synthetic",
+           "dtype": "f32-inner/f64-refinement" if args.precision == "mixed" else "f64",
+           "config": {"workload": f"{len(wls)} KGD instances, 1k-50k P2 triangles, {args.sweep_steps} steps each",
+                      "slots": args.slots, "autotuned": bool(args.autotune)},
+           "makespan_s": span, "instance_steps_per_s": sum(r["steps_done"] for r in recs) / span,
+           "completed": summ.get("completed"), "failed": summ.get("failed"),
+           "peak_running": st["peak_running"], "autotune_s": t_tune,
+           "tuned": tuner.report() if tuner else None, "clocks": clocks}
+    print(json.dumps(out))
+
+
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
@@ -447,9 +550,21 @@ def main():
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=4)
     ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--mode", default="newton", choices=["newton", "serve", "sweep"])
+    ap.add_argument("--slots", type=int, default=8)
+    ap.add_argument("--serve-requests", dest="serve_requests", type=int, default=0)
+    ap.add_argument("--serve-rate", dest="serve_rate", type=float, default=200.0)
+    ap.add_argument("--serve-steps", dest="serve_steps", type=int, default=5)
+    ap.add_argument("--sweep-count", dest="sweep_count", type=int, default=256)
+    ap.add_argument("--sweep-steps", dest="sweep_steps", type=int, default=10)
+    ap.add_argument("--autotune", type=int, default=1)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+    elif args.mode == "serve":
+        run_serve(args)
+    elif args.mode == "sweep":
+        run_sweep(args)
     else:
         run_ours(args)
 

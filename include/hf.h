@@ -92,7 +92,7 @@ typedef struct {
 enum { HF_PREC_FP64 = 0, HF_PREC_MIXED = 1 };
 typedef struct {
   int precision;        /* HF_PREC_FP64 or HF_PREC_MIXED (FP32 SpMV/ILU in FP64 IR) */
-  int restart;          /* GMRES restart length m (1..30) */
+  int restart;          /* GMRES restart length m (1..96) */
   int max_iters;        /* cap on GMRES iterations per Newton step (all cycles) */
   double rtol;          /* GMRES: ||J d + R|| <= rtol ||R|| */
   double inner_rtol;    /* mixed: reduction asked of each FP32 inner solve */
@@ -100,6 +100,8 @@ typedef struct {
   int fluid_scaling;    /* 1: scale pressure rows by c^n (remark in Sec. 3) */
   double newton_tol;    /* relative-increment tolerance of hf_newton_step */
   int use_graphs;       /* 1: capture each GMRES cycle in a CUDA graph */
+  int coarse;           /* 1: add the rigid-body coarse correction to the preconditioner */
+  int coarse_max;       /* bound on the coarse unknowns (16..4096): sets the aggregate size */
 } hf_solver_opts;
 
 /* Report of one Newton iteration (Sec. 3: convergence on the Euclidean norms
@@ -193,8 +195,11 @@ hf_status hf_solve_linear(hf_mesh* h, const double* rhs, double* d, hf_newton_re
  * without graphs).  hf_get_kernel_times returns the accumulated milliseconds
  * and launch counts since profiling was switched on, per class:
  * 0 SpMV (Krylov precision), 1 preconditioner apply, 2 Gram-Schmidt + norm,
- * 3 ILU factorisation, 4 assembly (facet terms + residual), 5 FP64 SpMV of the
- * refinement residual, 6 Newton update, 7 unused.  ms and launches hold 8. */
+ * 3 ILU factorisation (and the coarse matrix), 4 assembly (facet terms +
+ * residual), 5 FP64 SpMV of the refinement residual, 6 Newton update,
+ * 7 the rest of the preconditioner (coarse restriction, solve and
+ * prolongation; pressure rows).  Class 1 is the ILU(0) apply alone.  ms and
+ * launches hold 8. */
 hf_status hf_set_profiling(hf_mesh* h, int on);
 hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
 /* Structure counts: [0] elements, [1] interior facet slots (element-side pairs
@@ -203,7 +208,8 @@ hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
  * unknowns, [7] facets, [8] kernel launches issued by the library in this
  * process so far, [9] CUDA error met when reading timing events recorded
  * inside a captured GMRES cycle (0: none; graph cycles then go untimed),
- * [10] device bytes the handle holds, [11..15] zero.  st holds 16. */
+ * [10] device bytes the handle holds, [11] coarse unknowns in use (0: one
+ * level), [12] elements per coarse aggregate, [13..15] zero.  st holds 16. */
 hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
 
 const char* hf_last_error(const hf_mesh* h);
@@ -266,15 +272,36 @@ void hf_default_step_opts(hf_step_opts* o);
  * sub-step), any CUDA or state error as returned by the calls above. */
 hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* rep);
 
+/* Aggregate of each element (caller's element order) in the coarse level of
+ * the preconditioner: the preconditioner is M^-1 = B^-1 + Phi A0^-1 Phi^T,
+ * B the block-Jacobi ILU(0) of the subdomains, Phi the rigid-body modes of
+ * each aggregate (translations and infinitesimal rotations about its
+ * centre) on its elements' displacement unknowns, zero on Dirichlet rows,
+ * and A0 = Phi^T J_base Phi with J_base the linear part of the tangent
+ * (bulk and intact-facet blocks).  The paper has no coarse level (its
+ * subdomain solver is direct, Sec. 3); it is added here because the
+ * one-level iteration count grows with the mesh.  agg_of_elem holds n_elems. */
+hf_status hf_get_aggregates(const hf_mesh* h, int32_t* agg_of_elem);
+
+/* The coarse operator of the preconditioner (diagnostics): *nc coarse
+ * unknowns (call with NULL arrays first), A0 and its inverse as used
+ * (nc x nc, row-major, row/column index = aggregate * n_modes + mode), and per
+ * aggregate its centre (dim values, padded to 3) and size H, in geo (4 per
+ * aggregate).  Mode k < dim is the translation along axis k; the rotations
+ * (in the planes (0,1) [, (1,2), (2,0)]) take u_a = -X_b, u_b = X_a with
+ * X = (x - centre) / H. */
+hf_status hf_get_coarse_operator(hf_mesh* h, int64_t* nc, double* A0, double* A0inv, double* geo);
+
 /* Unknown counts of the system a descriptor defines, without a handle:
  * n_u = n_elems * nen * dim displacements, n_p pressure unknowns (the
  * distinct nodes of crackable interior facets). */
 hf_status hf_mesh_sizes(const hf_mesh_desc* desc, int64_t* n_u, int64_t* n_p);
 
 /* Upper bound on the device memory a handle for this mesh holds once it has
- * been created and stepped with the given Jacobi block size (both solver
- * precisions, the step snapshot included); read with hf_get_stats [10]. */
-hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, int jacobi_block, int64_t* bytes);
+ * been created, given these solver options (NULL: the defaults) and stepped
+ * (both solver precisions, the step snapshot included); read with
+ * hf_get_stats [10]. */
+hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, const hf_solver_opts* opts, int64_t* bytes);
 
 /* ------------------------------------------------------------ serving */
 

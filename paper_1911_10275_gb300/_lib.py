@@ -34,7 +34,8 @@ class hf_mesh_desc(C.Structure):
 class hf_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int),
                 ("rtol", C.c_double), ("inner_rtol", C.c_double), ("jacobi_block", C.c_int),
-                ("fluid_scaling", C.c_int), ("newton_tol", C.c_double), ("use_graphs", C.c_int)]
+                ("fluid_scaling", C.c_int), ("newton_tol", C.c_double), ("use_graphs", C.c_int),
+                ("coarse", C.c_int), ("coarse_max", C.c_int)]
 
 
 class hf_newton_report(C.Structure):
@@ -115,7 +116,9 @@ SIGNATURES = {
     "hf_default_step_opts": (None, [C.POINTER(hf_step_opts)]),
     "hf_advance_step": (C.c_int, [_H, C.POINTER(hf_step_opts), C.POINTER(hf_step_report)]),
     "hf_mesh_sizes": (C.c_int, [C.POINTER(hf_mesh_desc), _i64p, _i64p]),
-    "hf_estimate_device_bytes": (C.c_int, [C.POINTER(hf_mesh_desc), C.c_int, _i64p]),
+    "hf_get_aggregates": (C.c_int, [_H, _i32p]),
+    "hf_get_coarse_operator": (C.c_int, [_H, _i64p, _dp, _dp, _dp]),
+    "hf_estimate_device_bytes": (C.c_int, [C.POINTER(hf_mesh_desc), C.POINTER(hf_solver_opts), _i64p]),
     "hf_runtime_create": (C.c_int, [C.POINTER(hf_runtime_opts), C.POINTER(C.c_void_p)]),
     "hf_runtime_destroy": (C.c_int, [C.c_void_p]),
     "hf_runtime_submit": (C.c_int, [C.c_void_p, C.POINTER(hf_request), _i64p]),
@@ -124,7 +127,7 @@ SIGNATURES = {
     "hf_runtime_stats": (C.c_int, [C.c_void_p, _i64p]),
     "hf_runtime_now": (C.c_double, [C.c_void_p]),
 }
-KERNEL_CLASSES = ["spmv", "precond", "orth", "factor", "assembly", "spmv64", "update", "unused"]
+KERNEL_CLASSES = ["spmv", "precond", "orth", "factor", "assembly", "spmv64", "update", "precond_aux"]
 
 _lib = None
 
@@ -195,10 +198,13 @@ def hf_mesh_sizes(m):
     return nu.value, np_.value
 
 
-def hf_estimate_device_bytes(m, jacobi_block=32):
+def hf_estimate_device_bytes(m, **solver):
+    """Device-memory bound of a handle for mesh m with these solver options
+    (keyword arguments of hf_set_solver; the defaults otherwise)."""
     d, keep = desc_of(m)
     b = C.c_int64()
-    st = load().hf_estimate_device_bytes(C.byref(d), int(jacobi_block), C.byref(b))
+    o = solver_opts(**solver)
+    st = load().hf_estimate_device_bytes(C.byref(d), C.byref(o), C.byref(b))
     if st != HF_OK:
         raise HFError(st, "hf_estimate_device_bytes")
     return b.value
@@ -361,6 +367,24 @@ class HFMesh:
         self._check(self.lib.hf_apply_preconditioner(self.h, _ptr(x, C.c_double), _ptr(z, C.c_double)))
         return z
 
+    def hf_get_aggregates(self):
+        a = np.zeros(self._keep[1].shape[0], np.int32)
+        self._check(self.lib.hf_get_aggregates(self.h, _ptr(a, C.c_int32)))
+        return a
+
+    def hf_get_coarse_operator(self):
+        """(A0, A0^-1, geo) of the coarse level: geo[g] = centre (3) and size."""
+        nc = C.c_int64()
+        self._check(self.lib.hf_get_coarse_operator(self.h, C.byref(nc), None, None, None))
+        n = nc.value
+        A0 = np.zeros((n, n))
+        inv = np.zeros((n, n))
+        nagg = n // (3 if self.dim == 2 else 6)
+        geo = np.zeros((nagg, 4))
+        self._check(self.lib.hf_get_coarse_operator(self.h, C.byref(nc), _ptr(A0, C.c_double), _ptr(inv, C.c_double),
+                                                    _ptr(geo, C.c_double)))
+        return A0, inv, geo
+
     def hf_set_profiling(self, on=True):
         self._check(self.lib.hf_set_profiling(self.h, int(bool(on))))
 
@@ -374,7 +398,8 @@ class HFMesh:
         st = np.zeros(16, np.int64)
         self._check(self.lib.hf_get_stats(self.h, _ptr(st, C.c_int64)))
         keys = ["elements", "interior_slots", "subdomain_slots", "levels_max", "subdomains", "nl_faces",
-                "n_p", "faces", "kernel_launches", "graph_timing_error", "device_bytes"]
+                "n_p", "faces", "kernel_launches", "graph_timing_error", "device_bytes", "coarse_unknowns",
+                "aggregate_size"]
         return dict(zip(keys, (int(x) for x in st)))
 
     def hf_solve_linear(self, rhs):

@@ -10,7 +10,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libhfgb300.so")
-SOURCES = ["hf_api.cu", "hf_assembly.cu", "hf_solve.cu", "hf_noalloc.cu", "hf_runtime.cu"]
+SOURCES = ["hf_api.cu", "hf_assembly.cu", "hf_solve.cu", "hf_noalloc.cu", "hf_runtime.cu", "hf_coarse.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-fno-strict-aliasing"]
 

@@ -431,6 +431,7 @@ static hf_status rebuild_rows(hf_mesh* h, const std::vector<int>& elems) {
   if (h->dim == 2) launch_build_rows<2>(h->d, h->q, h->d_elist, (int)elems.size(), h->J64.dg, h->J64.off, h->stream);
   else launch_build_rows<3>(h->d, h->q, h->d_elist, (int)elems.size(), h->J64.dg, h->J64.off, h->stream);
   h->j32_valid = false;
+  h->coarse_dirty = true;
   for (int e : elems) h->sd_dirty.push_back(h->sd_of[e]);
   return check_cuda(h, cudaGetLastError(), "build_rows");
 }
@@ -442,6 +443,10 @@ static hf_status refactor(hf_mesh* h) {
   sds.erase(std::unique(sds.begin(), sds.end()), sds.end());
   if (!h->j32_valid && h->opts.precision == HF_PREC_MIXED) convert_j32(h);
   factor_subdomains(h, sds);
+  if (h->opts.coarse) {
+    hf_status s = coarse_refactor(h);
+    if (s) return s;
+  }
   h->sd_dirty.clear();
   return check_cuda(h, cudaGetLastError(), "factor");
 }
@@ -474,6 +479,8 @@ void hf_default_solver_opts(hf_solver_opts* o) {
   o->fluid_scaling = 1;
   o->newton_tol = 1e-10;
   o->use_graphs = 0;
+  o->coarse = 1;
+  o->coarse_max = 2048;
 }
 
 const char* hf_last_error(const hf_mesh* h) { return h ? h->err.c_str() : "null handle"; }
@@ -745,6 +752,7 @@ hf_status hf_mesh_create(const hf_mesh_desc* desc, void* cuda_stream, hf_mesh** 
   if (solver_alloc(h)) return fail(HF_ERR_OOM, h->err);
   if (dim == 2) launch_geometry<2>(d, h->stream);
   else launch_geometry<3>(d, h->stream);
+  if (coarse_layout(h)) return fail(HF_ERR_OOM, h->err);
   double one = 1.0;
   cudaMemcpyAsync(d.scal, &one, sizeof(double), cudaMemcpyHostToDevice, h->stream);
   cudaError_t e = cudaStreamSynchronize(h->stream);
@@ -814,13 +822,23 @@ hf_status hf_set_injection(hf_mesh* h, double mu, double Q0, int64_t n_inj, cons
 
 hf_status hf_set_solver(hf_mesh* h, const hf_solver_opts* o) {
   HF_GUARD(h);
-  if (!o || (o->precision != HF_PREC_FP64 && o->precision != HF_PREC_MIXED) || o->restart < 1 || o->restart > 30 ||
-      o->max_iters < 0 || !(o->rtol > 0) || !(o->inner_rtol > 0) || o->jacobi_block < 1)
+  if (!o || (o->precision != HF_PREC_FP64 && o->precision != HF_PREC_MIXED) || o->restart < 1 || o->restart > GM_MAX ||
+      o->max_iters < 0 || !(o->rtol > 0) || !(o->inner_rtol > 0) || o->jacobi_block < 1 || o->coarse < 0 ||
+      o->coarse > 1 || o->coarse_max < 16 || o->coarse_max > 4096)
     return set_error(h, HF_ERR_INVALID_ARG, "solver options out of range");
   bool regroup = std::min(256, o->jacobi_block) != h->G;
   bool rescale = o->fluid_scaling != h->opts.fluid_scaling;
+  bool relayout = o->coarse_max != h->opts.coarse_max || o->coarse != h->opts.coarse;
   h->opts = *o;
   invalidate_graphs(h);
+  {
+    hf_status s = krylov_basis_alloc(h, o->restart);
+    if (s) return s;
+  }
+  if (relayout) {
+    hf_status s = coarse_layout(h);
+    if (s) return s;
+  }
   if (regroup) {
     hf_status s = build_subdomains(h, o->jacobi_block);
     if (s) return s;
@@ -1154,7 +1172,9 @@ hf_status hf_get_stats(const hf_mesh* h, int64_t* st) {
   st[8] = total_launches();
   st[9] = h->prof.graph_timing_error;
   st[10] = h->bytes_allocated;
-  for (int i = 11; i < 16; ++i) st[i] = 0;
+  st[11] = h->opts.coarse ? h->nc : 0;
+  st[12] = h->agg_size;
+  for (int i = 13; i < 16; ++i) st[i] = 0;
   return HF_OK;
 }
 
@@ -1270,6 +1290,22 @@ static hf_status desc_counts(const hf_mesh_desc* desc, long long* np_out, long l
   return HF_OK;
 }
 
+hf_status hf_get_aggregates(const hf_mesh* h, int32_t* agg_of_elem) {
+  if (!h || !agg_of_elem || h->agg_size < 1) return HF_ERR_INVALID_ARG;
+  for (long long e = 0; e < h->ne; ++e) agg_of_elem[e] = h->ext2int[e] / h->agg_size;
+  return HF_OK;
+}
+
+hf_status hf_get_coarse_operator(hf_mesh* h, int64_t* nc, double* A0, double* A0inv, double* geo) {
+  HF_GUARD(h);
+  if (nc) *nc = h->opts.coarse ? h->nc : 0;
+  if (!A0 && !A0inv && !geo) return HF_OK;
+  hf_status s;
+  if ((s = assemble_nl(h))) return s;
+  if ((s = refactor(h))) return s;
+  return coarse_rebuild_copy(h, A0, A0inv, geo);
+}
+
 hf_status hf_mesh_sizes(const hf_mesh_desc* desc, int64_t* n_u, int64_t* n_p) {
   long long np = 0, ncrack = 0;
   hf_status s = desc_counts(desc, &np, &ncrack);
@@ -1279,9 +1315,16 @@ hf_status hf_mesh_sizes(const hf_mesh_desc* desc, int64_t* n_u, int64_t* n_p) {
   return HF_OK;
 }
 
-hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, int jacobi_block, int64_t* bytes) {
+hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, const hf_solver_opts* opts, int64_t* bytes) {
   long long np = 0, ncrack = 0;
   if (!bytes || desc_counts(desc, &np, &ncrack) != HF_OK) return HF_ERR_INVALID_ARG;
+  hf_solver_opts o;
+  hf_default_solver_opts(&o);
+  if (opts) o = *opts;
+  const int jacobi_block = o.jacobi_block;
+  // the bases are sized for the longest cycle the handle has been given: the
+  // default at creation, then this one
+  const long long mres = std::max(1, std::min(GM_MAX, std::max(o.restart, 30)));
   const long long dim = desc->dim, ne = desc->n_elems, nf = desc->n_faces, nn = desc->n_nodes;
   const long long nen = dim == 2 ? 6 : 10, ned = nen * dim, nfn = dim == 2 ? 3 : 6, nfr = nfn * dim, nsl = dim + 1;
   const long long nld = 4 * nfn * nfn + 3 * nfn, lus = ned * ned + nsl * ned * nfr;
@@ -1306,10 +1349,18 @@ hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, int jacobi_block, i
   add(ne * 8); add(ne * 8); add(ne * 8); add(nsd * 8); add(nsd * 8);
   add(std::max(ncrack, 64LL) * 4);
   // solver workspace of both precisions
-  add(ldv * 31 * 8); for (int i = 0; i < 5; ++i) add(N * 8);
-  add(ldv * 31 * 4); for (int i = 0; i < 5; ++i) add(N * 4);
+  add(ldv * (mres + 1) * 8); for (int i = 0; i < 5; ++i) add(N * 8);
+  add(ldv * (mres + 1) * 4); for (int i = 0; i < 5; ++i) add(N * 4);
   add(ne * lus * 8); add(ne * lus * 4); add(std::max(np, 1LL) * 8); add(std::max(np, 1LL) * 4);
-  add(nmat * 4); add(152 * 4 * 32 * 8); add((long long)sizeof(GmresState));
+  add(nmat * 4); add(152 * 4 * GM_LD * 8); add((long long)sizeof(GmresState));
+  // coarse level (largest layout the options allow: coarse_max = 4096 at most)
+  {
+    int cA = 0, cnagg = 0, cnc = 0;
+    coarse_sizes(ne, (int)dim, o.coarse ? o.coarse_max : 2048, &cA, &cnagg, &cnc);
+    const long long nc2 = (long long)cnc * cnc;
+    add(cnagg * 4 * 8); add(nu * 8); add(nu * 4); add(nc2 * 8); add(nc2 * 8); add(nc2 * 4); add(8);
+    add(cnc * 8); add(cnc * 8); add(cnc * 4); add(cnc * 4);
+  }
   // time-step snapshot
   add(N * 8); add(nfn * nf * 8);
   *bytes = t;

@@ -43,15 +43,18 @@ template <typename T> struct Krylov {
   T* b = nullptr;        // right-hand side
   T* lu = nullptr;       // ILU records
   T* sinv = nullptr;     // pressure-row Schur diagonal (inverse)
+  T* cc = nullptr;       // coarse residual Phi^T r
+  T* cy = nullptr;       // coarse solution A0^-1 Phi^T r
   long long ldv = 0;
 };
 
-// device scalars of the GMRES driver (one record, double precision)
+// longest GMRES cycle, and the leading dimension of its Hessenberg matrix
+constexpr int GM_MAX = 96;
+constexpr int GM_LD = GM_MAX + 1;
+
+// device scalars of the GMRES driver (one record, double precision); the
+// host reads back only the leading scalars
 struct GmresState {
-  double H[31 * 30];     // Hessenberg, rotated in place (column-major, ld 31)
-  double g[31];
-  double cs[30], sn[30];
-  double y[30];
   double inv_h;          // 1 / h(j+1, j)
   double beta;           // residual norm of the cycle start
   double tol_abs;        // absolute stopping threshold for |g(j+1)|
@@ -60,11 +63,15 @@ struct GmresState {
   int jlast;
   int iters;
   int pad;
+  double g[GM_LD];
+  double cs[GM_MAX], sn[GM_MAX];
+  double y[GM_MAX];
+  double H[GM_LD * GM_MAX];  // Hessenberg, rotated in place (column-major, ld GM_LD)
 };
 
 // event-timed kernel classes (profiling mode)
 enum ProfKind { PK_SPMV = 0, PK_PREC = 1, PK_ORTH = 2, PK_FACTOR = 3, PK_ASSEMBLY = 4, PK_SPMV64 = 5,
-                PK_UPDATE = 6, PK_COUNT = 8 };
+                PK_UPDATE = 6, PK_PREC_AUX = 7, PK_COUNT = 8 };
 constexpr int PROF_EVENTS = 256;
 // event pair recorded as graph nodes inside a captured GMRES cycle; j is the
 // Arnoldi step it belongs to (-1: once per cycle)
@@ -142,6 +149,7 @@ struct hf_mesh {
   hfk::Krylov<double> K64;
   hfk::Krylov<float> K32;
   int red_blocks = 0;
+  int m_alloc = 0;             // GMRES cycle length the Krylov bases hold
 
   // parameters
   double E = 0, nu_p = 0, sigma_c = 0, delta_c = 0, b_stab = 10.0;
@@ -158,6 +166,18 @@ struct hf_mesh {
   hfk::Prof prof;
   long long n_interior_slots = 0, n_subdomain_slots = 0;
 
+  // coarse level of the preconditioner (hf_coarse.cu)
+  int agg_size = 0, nagg = 0, nc = 0;       // elements per aggregate, aggregates, coarse unknowns
+  bool coarse_dirty = true;                 // J_base changed since A0 was inverted
+  double* agg_geo = nullptr;                // [g*4]: centre (dim), size
+  double* rc64 = nullptr;                   // [e*ned + t]: scaled coordinate k of the node of slot t
+  float* rc32 = nullptr;
+  double* A0a = nullptr;                    // nc x nc, Gauss-Jordan ping-pong buffers
+  double* A0b = nullptr;
+  double* A0inv64 = nullptr;                // the buffer holding A0^-1
+  float* A0inv32 = nullptr;
+  double* d_cthr = nullptr;                 // pivot threshold
+
   // start-of-step snapshot of hf_advance_step (restored when a step is cut)
   double* snap_X = nullptr;
   double* snap_wold = nullptr;
@@ -171,8 +191,16 @@ namespace hfk {
 // aligned, released by dev_free or at hf_mesh_destroy
 void* dev_alloc(hf_mesh* h, size_t bytes);
 void dev_free(hf_mesh* h, void* p);
+// coarse level (hf_coarse.cu)
+void coarse_sizes(long long ne, int dim, int coarse_max, int* A, int* nagg, int* nc);
+hf_status coarse_layout(hf_mesh* h);
+hf_status coarse_refactor(hf_mesh* h);
+hf_status coarse_rebuild_copy(hf_mesh* h, double* A0_host, double* inv_host, double* geo_host);
+template <typename T, int DIM> void coarse_pre(hf_mesh* h, const Krylov<T>& K, const T* rin, const int* skip);
+template <typename T, int DIM> void coarse_post(hf_mesh* h, const Krylov<T>& K, T* z, const int* skip);
 // solver side (hf_solve.cu)
 hf_status solver_alloc(hf_mesh* h);
+hf_status krylov_basis_alloc(hf_mesh* h, int m);
 void convert_j32(hf_mesh* h);
 void factor_subdomains(hf_mesh* h, const std::vector<int>& sds);
 hf_status residual(hf_mesh* h, const double* X, double* R);

@@ -237,7 +237,7 @@ hf_status hf_runtime_submit(hf_runtime* rt, const hf_request* r, int64_t* id) {
   j->inj_dofs = copy_of(r->inj_dofs, r->n_inj);
   j->inj_weights = copy_of(r->inj_weights, r->n_inj);
   int64_t est = 0, nu = 0, np = 0;
-  if (hf_estimate_device_bytes(&j->desc, r->solver.jacobi_block, &est) != HF_OK ||
+  if (hf_estimate_device_bytes(&j->desc, &r->solver, &est) != HF_OK ||
       hf_mesh_sizes(&j->desc, &nu, &np) != HF_OK)
     return HF_ERR_INVALID_ARG;
   j->alpha0 = copy_of(r->alpha0, d.n_faces);

@@ -19,6 +19,7 @@
 //  * Mixed precision: FP32 matrix, factor and Krylov vectors inside FP64
 //    iterative refinement (residual and update in FP64).
 #include <atomic>
+#include <cstddef>
 #include <mutex>
 #include <algorithm>
 #include <cmath>
@@ -719,36 +720,40 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
 template <typename T, int DIM>
 __global__ void k_prec_p(DevMesh m, const T* __restrict__ rin, const double* scale, T* vout, const T* __restrict__ sinv,
                          T* z, const int* skip) {
+  // one warp per pressure row: the lanes share the (incident facet, face
+  // node) terms of C z_u, so the row's dependent loads are not serialised
   using S = Shape<DIM>;
   using L = NL<DIM>;
   constexpr int F = S::nfn, NED = S::ned;
   if (skip && *skip) return;
-  int g = blockIdx.x * blockDim.x + threadIdx.x;
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (g >= m.np) return;
   T sc = scale ? (T)(*scale) : (T)1;
   T r = rin[m.nu + g] * sc;
-  if (vout) vout[m.nu + g] = r;
+  if (lane == 0 && vout) vout[m.nu + g] = r;
   if (!m.p_active[g]) {
-    z[m.nu + g] = r;
+    if (lane == 0) z[m.nu + g] = r;
     return;
   }
+  const int t0 = m.pinc_ptr[g], nt = (m.pinc_ptr[g + 1] - t0) * F;
   double acc = 0.0;
-  for (int t = m.pinc_ptr[g]; t < m.pinc_ptr[g + 1]; ++t) {
-    int f = m.pinc_face[t];
+  for (int q = lane; q < nt; q += 32) {
+    const int t = t0 + q / F, b = q % F;
+    const int f = m.pinc_face[t];
     if (!m.beta[f]) continue;
-    int ga = m.pinc_a[t];
-    const double* rec = m.nl + (long long)f * S::nld;
-    int em = m.fe[f], ep = m.fe[m.nf + f];
-    for (int b = 0; b < F; ++b) {
-      int lm = m.loc_m[b * m.nf + f], lp = m.loc_p[b * m.nf + f];
-      double jn = 0.0;
-      for (int k = 0; k < DIM; ++k)
-        jn += m.fnormal[k * m.nf + f] *
-              ((double)z[(long long)ep * NED + lp * DIM + k] - (double)z[(long long)em * NED + lm * DIM + k]);
-      acc += rec[L::Cs + ga * F + b] * jn;
-    }
+    const int ga = m.pinc_a[t];
+    const int em = m.fe[f], ep = m.fe[m.nf + f];
+    const int lm = m.loc_m[b * m.nf + f], lp = m.loc_p[b * m.nf + f];
+    double jn = 0.0;
+#pragma unroll
+    for (int k = 0; k < DIM; ++k)
+      jn += m.fnormal[k * m.nf + f] *
+            ((double)z[(long long)ep * NED + lp * DIM + k] - (double)z[(long long)em * NED + lm * DIM + k]);
+    acc += m.nl[(long long)f * S::nld + L::Cs + ga * F + b] * jn;
   }
-  z[m.nu + g] = (T)(((double)r - m.scal[0] * acc) * (double)sinv[g]);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if (lane == 0) z[m.nu + g] = (T)(((double)r - m.scal[0] * acc) * (double)sinv[g]);
 }
 
 // ------------------------------------------------------------------ reductions
@@ -802,75 +807,85 @@ __device__ double block_sum_partials(const double* partial, int n, int stride, i
   return t;
 }
 
-// multi-dot: H[:, j] = V[:, 0..j]^T w
+// multi-dot: H[:, j] = V[:, 0..j]^T w, in chunks of 32 columns (w is
+// re-read per chunk, from L2)
 template <typename T>
 __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long ldv, int j, const T* __restrict__ w,
                                              long long n, double* partial, int* counter, GmresState* gs) {
   if (gs->done) return;
   __shared__ double sm[RB / 32][32];
   __shared__ bool last;
-  int ncols = j + 1;
-  T acc[32];
-#pragma unroll
-  for (int c = 0; c < 32; ++c) acc[c] = (T)0;
+  const int ncols = j + 1;
   using VT = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
   const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nv = n / VN;
-  for (long long iv = tid; iv < nv; iv += stride) {
-    VT wv = reinterpret_cast<const VT*>(w)[iv];
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < ncols) acc[c] += Vec<T>::dot(reinterpret_cast<const VT*>(V + c * ldv)[iv], wv);
-  }
-  for (long long i = nv * VN + tid; i < n; i += stride) {
-    T wv = w[i];
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < ncols) acc[c] += V[c * ldv + i] * wv;
-  }
-  // block reduction by transposition: warp w writes its 32 accumulators as
-  // row lane of a 32x32 tile; lane c then adds column c (working precision,
-  // 32 adds) and the 8 warp results meet in double
-  constexpr int CH = sizeof(T) == 4 ? 32 : 16;   // columns per pass (static smem < 48 KB)
+  constexpr int CH = sizeof(T) == 4 ? 32 : 16;   // columns per transpose pass (static smem < 48 KB)
   __shared__ T tile[RB / 32][32][CH + 1];
-  int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  for (int q0 = 0; q0 < ncols; q0 += 32) {
+    const int nq = min(32, ncols - q0);
+    const T* Vq = V + (long long)q0 * ldv;
+    T acc[32];
 #pragma unroll
-  for (int c0 = 0; c0 < 32; c0 += CH) {
+    for (int c = 0; c < 32; ++c) acc[c] = (T)0;
+    for (long long iv = tid; iv < nv; iv += stride) {
+      VT wv = reinterpret_cast<const VT*>(w)[iv];
 #pragma unroll
-    for (int c = 0; c < CH; ++c) tile[warp][lane][c] = acc[c0 + c];
-    __syncwarp();
-    if (lane < CH) {
-      T colsum = (T)0;
-#pragma unroll
-      for (int l = 0; l < 32; ++l) colsum += tile[warp][l][lane];
-      sm[warp][c0 + lane] = (double)colsum;
+      for (int c = 0; c < 32; ++c)
+        if (c < nq) acc[c] += Vec<T>::dot(reinterpret_cast<const VT*>(Vq + c * ldv)[iv], wv);
     }
-    __syncwarp();
-  }
-  __syncthreads();
-  if (threadIdx.x < ncols) {
-    double s = 0.0;
-    for (int wq = 0; wq < RB / 32; ++wq) s += sm[wq][threadIdx.x];
-    partial[blockIdx.x * 32 + threadIdx.x] = s;
+    for (long long i = nv * VN + tid; i < n; i += stride) {
+      T wv = w[i];
+#pragma unroll
+      for (int c = 0; c < 32; ++c)
+        if (c < nq) acc[c] += Vq[c * ldv + i] * wv;
+    }
+    // block reduction by transposition: warp w writes its 32 accumulators as
+    // row lane of a 32x32 tile; lane c then adds column c (working precision,
+    // 32 adds) and the warp results meet in double
+#pragma unroll
+    for (int c0 = 0; c0 < 32; c0 += CH) {
+#pragma unroll
+      for (int c = 0; c < CH; ++c) tile[warp][lane][c] = acc[c0 + c];
+      __syncwarp();
+      if (lane < CH) {
+        T colsum = (T)0;
+#pragma unroll
+        for (int l = 0; l < 32; ++l) colsum += tile[warp][l][lane];
+        sm[warp][c0 + lane] = (double)colsum;
+      }
+      __syncwarp();
+    }
+    __syncthreads();
+    if (threadIdx.x < nq) {
+      double s = 0.0;
+      for (int wq = 0; wq < RB / 32; ++wq) s += sm[wq][threadIdx.x];
+      partial[(long long)blockIdx.x * GM_LD + q0 + threadIdx.x] = s;
+    }
+    __syncthreads();
   }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
   __syncthreads();
   if (last) {
-    // one pass over all columns: thread (grp, c) sums rows b = grp, grp+8, ...
-    // of the partial table, then column c adds the 8 groups in order
+    // per chunk of 32 columns: thread (grp, c) sums rows b = grp, grp+8, ...
+    // of the partial table, then column c adds the groups in order
     __shared__ double red[RB / 32][32];
-    int c = threadIdx.x & 31, grp = threadIdx.x >> 5;
-    double sacc = 0.0;
-    for (int b = grp; b < (int)gridDim.x; b += RB / 32) sacc += __ldcg(partial + (long long)b * 32 + c);
-    red[grp][c] = sacc;
-    __syncthreads();
-    if (threadIdx.x < ncols) {
-      double tot = 0.0;
-      for (int g2 = 0; g2 < RB / 32; ++g2) tot += red[g2][threadIdx.x];
-      gs->H[j * 31 + threadIdx.x] = tot;
+    const int c = threadIdx.x & 31, grp = threadIdx.x >> 5;
+    for (int q0 = 0; q0 < ncols; q0 += 32) {
+      double sacc = 0.0;
+      if (q0 + c < ncols)
+        for (int b = grp; b < (int)gridDim.x; b += RB / 32) sacc += __ldcg(partial + (long long)b * GM_LD + q0 + c);
+      red[grp][c] = sacc;
+      __syncthreads();
+      if (threadIdx.x < 32 && q0 + (int)threadIdx.x < ncols) {
+        double tot = 0.0;
+        for (int g2 = 0; g2 < RB / 32; ++g2) tot += red[g2][threadIdx.x];
+        gs->H[j * GM_LD + q0 + threadIdx.x] = tot;
+      }
+      __syncthreads();
     }
     if (threadIdx.x == 0) *counter = 0;
   }
@@ -881,9 +896,9 @@ template <typename T>
 __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
                                              double* partial, int* counter, GmresState* gs, int mrest) {
   if (gs->done) return;
-  __shared__ T h[32];
-  int ncols = j + 1;
-  if (threadIdx.x < 32) h[threadIdx.x] = threadIdx.x < ncols ? (T)gs->H[j * 31 + threadIdx.x] : (T)0;
+  __shared__ T h[GM_MAX];
+  const int ncols = j + 1;
+  for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) h[c] = c < ncols ? (T)gs->H[j * GM_LD + c] : (T)0;
   __syncthreads();
   T acc_t = (T)0;
   using VT = typename Vec<T>::type;
@@ -892,17 +907,14 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
   const long long nv = n / VN;
   for (long long iv = tid; iv < nv; iv += stride) {
     VT ww = reinterpret_cast<const VT*>(w)[iv];
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < ncols) Vec<T>::axpy(ww, h[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
+#pragma unroll 8
+    for (int c = 0; c < ncols; ++c) Vec<T>::axpy(ww, h[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
     reinterpret_cast<VT*>(w)[iv] = ww;
     acc_t += Vec<T>::dot(ww, ww);
   }
   for (long long i = nv * VN + tid; i < n; i += stride) {
     T ww = w[i];
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < ncols) ww -= h[c] * V[c * ldv + i];
+    for (int c = 0; c < ncols; ++c) ww -= h[c] * V[c * ldv + i];
     w[i] = ww;
     acc_t += ww * ww;
   }
@@ -910,7 +922,7 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
   double nrm2 = block_sum_partials(partial, gridDim.x, 1, 0);
   if (threadIdx.x == 0) {
     double nrm = sqrt(nrm2);
-    double* hc = gs->H + j * 31;
+    double* hc = gs->H + j * GM_LD;
     for (int i = 0; i < j; ++i) {
       double a = hc[i], b = hc[i + 1];
       hc[i] = gs->cs[i] * a + gs->sn[i] * b;
@@ -951,17 +963,17 @@ __global__ void k_backsolve(GmresState* gs) {
   int jl = gs->jlast;
   for (int i = jl - 1; i >= 0; --i) {
     double s = gs->g[i];
-    for (int k = i + 1; k < jl; ++k) s -= gs->H[k * 31 + i] * gs->y[k];
-    double d = gs->H[i * 31 + i];
+    for (int k = i + 1; k < jl; ++k) s -= gs->H[k * GM_LD + i] * gs->y[k];
+    double d = gs->H[i * GM_LD + i];
     gs->y[i] = d != 0.0 ? s / d : 0.0;
   }
 }
 
 template <typename T>
 __global__ void k_combine(const T* __restrict__ V, long long ldv, long long n, const GmresState* gs, T* u) {
-  __shared__ T y[32];
-  int jl = gs->jlast;
-  if (threadIdx.x < 32) y[threadIdx.x] = threadIdx.x < jl ? (T)gs->y[threadIdx.x] : (T)0;
+  __shared__ T y[GM_MAX];
+  const int jl = gs->jlast;
+  for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) y[c] = c < jl ? (T)gs->y[c] : (T)0;
   __syncthreads();
   using VT = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
@@ -969,16 +981,13 @@ __global__ void k_combine(const T* __restrict__ V, long long ldv, long long n, c
   const long long nv = n / VN;
   for (long long iv = tid; iv < nv; iv += stride) {
     VT s = Vec<T>::zero();
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < jl) Vec<T>::fma(s, y[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
+#pragma unroll 8
+    for (int c = 0; c < jl; ++c) Vec<T>::fma(s, y[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
     reinterpret_cast<VT*>(u)[iv] = s;
   }
   for (long long i = nv * VN + tid; i < n; i += stride) {
     T s = (T)0;
-#pragma unroll
-    for (int c = 0; c < 32; ++c)
-      if (c < jl) s += y[c] * V[c * ldv + i];
+    for (int c = 0; c < jl; ++c) s += y[c] * V[c * ldv + i];
     u[i] = s;
   }
 }
@@ -1005,7 +1014,7 @@ __global__ void __launch_bounds__(RB) k_residual_start(const T* __restrict__ b, 
   if (threadIdx.x == 0) {
     double beta = sqrt(b2);
     gs->beta = beta;
-    for (int i = 0; i < 31; ++i) gs->g[i] = 0.0;
+    for (int i = 0; i < GM_LD; ++i) gs->g[i] = 0.0;
     gs->g[0] = beta;
     gs->inv_h = beta > 0.0 ? 1.0 / beta : 0.0;
     gs->tol_abs = tol_abs;
@@ -1189,13 +1198,32 @@ template <typename T> static T* dalloc(hf_mesh* h, size_t n) {
   return reinterpret_cast<T*>(dev_alloc(h, n * sizeof(T)));
 }
 
+// Krylov bases for cycles of up to m vectors (re-allocated when a longer
+// cycle is asked for)
+hf_status krylov_basis_alloc(hf_mesh* h, int m) {
+  m = std::max(1, std::min(GM_MAX, m));
+  if (m <= h->m_alloc) return HF_OK;
+  const long long ldv = h->K64.ldv;
+  dev_free(h, h->K64.V);
+  dev_free(h, h->K32.V);
+  h->K64.V = dalloc<double>(h, (size_t)ldv * (m + 1));
+  h->K32.V = dalloc<float>(h, (size_t)ldv * (m + 1));
+  if (!h->K64.V || !h->K32.V) {
+    h->m_alloc = 0;
+    return set_error(h, HF_ERR_OOM, "device allocation of the Krylov basis failed");
+  }
+  h->m_alloc = m;
+  return HF_OK;
+}
+
 hf_status solver_alloc(hf_mesh* h) {
   long long N = h->N;
-  int m = 30;
+  int m = std::max(1, std::min(GM_MAX, h->opts.restart));
   long long ldv = (N + 63) / 64 * 64;
   h->red_blocks = 152 * 4;
   h->K64.ldv = ldv;
   h->K32.ldv = ldv;
+  h->m_alloc = m;
   h->K64.V = dalloc<double>(h, (size_t)ldv * (m + 1));
   h->K64.w = dalloc<double>(h, N);
   h->K64.z = dalloc<double>(h, N);
@@ -1216,7 +1244,7 @@ hf_status solver_alloc(hf_mesh* h) {
   size_t nmat = (size_t)h->ne * (h->ned * h->ned + (h->dim + 1) * h->ned * h->nfr);
   h->J32.dg = dalloc<float>(h, nmat);
   h->J32.off = h->J32.dg + (size_t)h->ne * h->ned * h->ned;
-  h->d_partial = dalloc<double>(h, (size_t)h->red_blocks * 32);
+  h->d_partial = dalloc<double>(h, (size_t)h->red_blocks * GM_LD);
   h->d_gs = dalloc<GmresState>(h, 1);
   if (!h->K64.V || !h->K64.w || !h->K64.z || !h->K64.u || !h->K64.x || !h->K64.b || !h->K32.V ||
       !h->K32.w || !h->K32.z || !h->K32.u || !h->K32.x || !h->K32.b || !h->K64.lu || !h->K32.lu ||
@@ -1306,11 +1334,24 @@ static void precond(hf_mesh* h, const Krylov<T>& K, const T* rin, const double* 
   (void)vout;
   // warps (subdomains) per CTA: as many as keep at least two CTAs per SM busy
   int nsd = h->d.nsd;
+  const bool coarse = h->opts.coarse && h->nc > 0;
+  if (coarse) {
+    prof_begin(h, PK_PREC_AUX);
+    coarse_pre<T, DIM>(h, K, rin, skip);
+    prof_end(h);
+  }
+  prof_begin(h, PK_PREC);
   if (nsd >= 4 * 2 * 152) launch_apply<T, DIM, 4>(h, K.lu, rin, z, skip);
   else if (nsd >= 2 * 2 * 152) launch_apply<T, DIM, 2>(h, K.lu, rin, z, skip);
   else launch_apply<T, DIM, 1>(h, K.lu, rin, z, skip);
-  if (h->np > 0)
-    { note_launch(); k_prec_p<T, DIM><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d, rin, nullptr, nullptr, K.sinv, z, skip); }
+  prof_end(h);
+  if (coarse || h->np > 0) {
+    prof_begin(h, PK_PREC_AUX);
+    if (coarse) coarse_post<T, DIM>(h, K, z, skip);
+    if (h->np > 0)
+      { note_launch(); k_prec_p<T, DIM><<<(int)((h->np + 7) / 8), 256, 0, h->stream>>>(h->d, rin, nullptr, nullptr, K.sinv, z, skip); }
+    prof_end(h);
+  }
 }
 
 // one GMRES(m) cycle on x (V[0] and gs already set by k_residual_start)
@@ -1324,9 +1365,7 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
   for (int j = 0; j < mrest; ++j) {
     T* vj = K.V + (long long)j * K.ldv;
     h->prof.cap_j = j;
-    prof_begin(h, PK_PREC);
     precond<T, DIM>(h, K, vj, nullptr, nullptr, K.z, done);
-    prof_end(h);
     prof_begin(h, PK_SPMV);
     spmv<T, DIM, 0>(h, dg, off, K.z, K.w, done);
     prof_end(h);
@@ -1387,7 +1426,7 @@ struct CycleInfo {
 
 static hf_status read_gs(hf_mesh* h, CycleInfo* ci) {
   GmresState tmp;
-  cudaError_t e = cudaMemcpyAsync(&tmp, h->d_gs, sizeof(GmresState), cudaMemcpyDeviceToHost, h->stream);
+  cudaError_t e = cudaMemcpyAsync(&tmp, h->d_gs, offsetof(GmresState, g), cudaMemcpyDeviceToHost, h->stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
   prof_flush(h);
   if (e != cudaSuccess) return check_cuda(h, e, "gmres state read");
@@ -1403,7 +1442,7 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
   long long N = h->N;
   int rb = h->red_blocks;
   int* cnt = h->d_count + 4;
-  int mrest = std::max(1, std::min(30, o.restart));
+  int mrest = std::max(1, std::min(GM_MAX, std::min(o.restart, h->m_alloc)));
   // ||b||
   { note_launch(); k_norm2<double><<<rb, RB, 0, h->stream>>>(b, N, h->d_partial, cnt, h->d_red); }
   double bn2 = 0.0;

@@ -127,7 +127,7 @@ def test_block_diagonal_preconditioner_is_exact_on_its_blocks(name):
     element diagonal blocks: for x supported on non-adjacent elements,
     M^-1 (J x) returns x on those elements."""
     wl = cases()[name]
-    o, g, _ = _pair(wl, jacobi_block=1)
+    o, g, _ = _pair(wl, jacobi_block=1, coarse=0)
     m = wl.mesh
     nen, d = m.n_en, m.dim
     ned = nen * d

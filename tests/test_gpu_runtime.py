@@ -77,7 +77,7 @@ def test_device_bytes_within_estimate(make):
     g.hf_set_state(*wl.seed())
     g.hf_advance_step()
     used = g.hf_get_stats()["device_bytes"]
-    est = hf_estimate_device_bytes(wl.mesh, 16)
+    est = hf_estimate_device_bytes(wl.mesh, jacobi_block=16)
     assert used <= est <= 1.02 * used + 4096
     g.close()
 
@@ -135,7 +135,7 @@ def test_each_result_is_the_same_alone_and_in_the_mix():
 def test_admission_keeps_device_memory_within_budget():
     from paper_1911_10275_gb300 import HFRuntime, hf_estimate_device_bytes
     reqs = _mix()
-    est = [hf_estimate_device_bytes(wl.mesh, s["jacobi_block"]) for wl, s in reqs]
+    est = [hf_estimate_device_bytes(wl.mesh, **s) for wl, s in reqs]
     budget = int(2.2 * max(est))
     rt = HFRuntime(slots=4, hbm_budget_bytes=budget)
     res = _run(rt, reqs, steps=1)

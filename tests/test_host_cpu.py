@@ -26,14 +26,15 @@ def test_device_bound_grows_with_the_mesh_and_covers_the_matrices():
     prev = 0
     for n in (8, 16, 32):
         m = kgd_2d(n=n).mesh
-        b = hf_estimate_device_bytes(m, 32)
+        b = hf_estimate_device_bytes(m, jacobi_block=32)
         ne = m.n_elems
         # J in FP64 and FP32 plus both ILU record sets: 4 (12x12 + 3 * 12x6) values per element
         assert b >= ne * (144 + 216) * (8 + 4) * 2
         assert b > prev
         prev = b
     m = penny_3d(n=4).mesh
-    assert hf_estimate_device_bytes(m, 8) >= hf_estimate_device_bytes(m, 64)
+    assert hf_estimate_device_bytes(m, jacobi_block=8) >= hf_estimate_device_bytes(m, jacobi_block=64)
+    assert hf_estimate_device_bytes(m, restart=90) > hf_estimate_device_bytes(m, restart=30)
 
 
 def test_partition_is_balanced_complete_and_deterministic():
