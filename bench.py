@@ -103,6 +103,16 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+def solver_kw(args, prec, graphs=None):
+    """Solver options of the timed path: GMRES to a relative residual of 1e-8,
+    each precision with its own cycle length and Gram-Schmidt passes."""
+    mixed = prec == "mixed"
+    return dict(precision=prec, restart=args.restart if mixed else args.fp64_restart,
+                reorth=args.reorth if mixed else args.fp64_reorth, rtol=1e-8, inner_rtol=1e-3,
+                max_iters=args.max_iters, jacobi_block=args.jacobi_block, newton_tol=1e-8,
+                use_graphs=args.graphs if graphs is None else graphs, coarse=args.coarse)
+
+
 def make_problem(wl, precision, stream_ptr, G, restart):
     from paper_1911_10275_gb300 import HFMesh
     g = HFMesh.from_mesh(wl.mesh, stream=stream_ptr)
@@ -223,9 +233,7 @@ def run_ours(args):
     stream = torch.cuda.Stream(device=dev)
     prec = "mixed" if args.precision == "mixed" else "fp64"
     g = make_problem(wl, prec, stream.cuda_stream, args.jacobi_block, args.restart)
-    if args.graphs:
-        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
-                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=1)
+    g.hf_set_solver(**solver_kw(args, prec))
     U, P, al, be = wl.seed()
     g.hf_set_state(U, P, al, be)
     loop = NewtonLoop(g, wl)
@@ -258,15 +266,13 @@ def run_ours(args):
         # this driver/toolkit gave no timing for events recorded inside graphs:
         # time the kernels with events on the same state, graphs off, right after
         code = g.hf_get_stats()["graph_timing_error"]
-        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
-                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=0)
+        g.hf_set_solver(**solver_kw(args, prec, graphs=0))
         g.hf_set_profiling(True)
         for _ in range(2):
             loop.step()
         ktimes = g.hf_get_kernel_times()
         g.hf_set_profiling(False)
-        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
-                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=args.graphs)
+        g.hf_set_solver(**solver_kw(args, prec))
         timing_source = ("CUDA events over 2 Newton iterations right after the timed region, same state, "
                          f"graphs off (graph-node event timing unavailable: CUDA error {code})")
     stats = g.hf_get_stats()
@@ -305,8 +311,7 @@ def run_ours(args):
     # FP64 beside it on the same starting state (fewer steps)
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0:
-        g.hf_set_solver(precision="fp64", restart=args.restart, rtol=1e-8, max_iters=3000,
-                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=args.graphs)
+        g.hf_set_solver(**solver_kw(args, "fp64"))
         g.hf_set_state(U, P, al, be)
         l64 = NewtonLoop(g, wl)
         for _ in range(min(args.warmup, 2)):
@@ -322,9 +327,9 @@ def run_ours(args):
         ms64 = e0.elapsed_time(e1)
         fp64 = {"value": args.fp64_steps / (ms64 / 1000.0), "unit": UNIT, "steps": args.fp64_steps,
                 "ms_per_step": ms64 / args.fp64_steps,
-                "gmres_iters_per_newton": float(np.mean([r["gmres_iters"] for r in l64.reports]))}
-        g.hf_set_solver(precision=prec, restart=args.restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
-                        jacobi_block=args.jacobi_block, newton_tol=1e-8, use_graphs=args.graphs)
+                "gmres_iters_per_newton": float(np.mean([r["gmres_iters"] for r in l64.reports])),
+                "restart": args.fp64_restart, "reorth": args.fp64_reorth}
+        g.hf_set_solver(**solver_kw(args, prec))
 
     # roofline of the dominant kernel class, from the events of the timed region
     elt = 4 if prec == "mixed" else 8
@@ -351,7 +356,9 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-inner/f64-refinement" if prec == "mixed" else "f64",
         "data": "synthetic (seeded structured P2 mesh and seed crack)",
         "config": {"workload": wl.name, "dofs": int(g.N), "elements": int(wl.mesh.n_elems),
-                   "precision": prec, "gmres_rtol": 1e-8, "restart": args.restart,
+                   "precision": prec, "gmres_rtol": 1e-8, "restart": args.restart, "reorth": bool(args.reorth),
+                   "preconditioner": ("block-Jacobi ILU(0) + rigid-body coarse level (%d coarse unknowns)"
+                                      % stats.get("coarse_unknowns", 0)) if args.coarse else "block-Jacobi ILU(0)",
                    "jacobi_block": args.jacobi_block, "cuda_graphs": bool(args.graphs),
                    "parallelism": f"replicas x{world}",
                    "l2": "working set larger than L2 (matrix + factor %.2f GB per replica)" %
@@ -544,7 +551,12 @@ def main():
     ap.add_argument("--config", default="c3")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--jacobi-block", dest="jacobi_block", type=int, default=32)
-    ap.add_argument("--restart", type=int, default=30)
+    ap.add_argument("--restart", type=int, default=60)
+    ap.add_argument("--reorth", type=int, default=1)
+    ap.add_argument("--fp64-restart", dest="fp64_restart", type=int, default=60)
+    ap.add_argument("--fp64-reorth", dest="fp64_reorth", type=int, default=0)
+    ap.add_argument("--max-iters", dest="max_iters", type=int, default=8000)
+    ap.add_argument("--coarse", type=int, default=1)
     ap.add_argument("--graphs", type=int, default=1)
     ap.add_argument("--fp64-steps", dest="fp64_steps", type=int, default=3)
     ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=4)

@@ -92,7 +92,7 @@ typedef struct {
 enum { HF_PREC_FP64 = 0, HF_PREC_MIXED = 1 };
 typedef struct {
   int precision;        /* HF_PREC_FP64 or HF_PREC_MIXED (FP32 SpMV/ILU in FP64 IR) */
-  int restart;          /* GMRES restart length m (1..96) */
+  int restart;          /* GMRES restart length m (1..96; default 60) */
   int max_iters;        /* cap on GMRES iterations per Newton step (all cycles) */
   double rtol;          /* GMRES: ||J d + R|| <= rtol ||R|| */
   double inner_rtol;    /* mixed: reduction asked of each FP32 inner solve */
@@ -102,6 +102,8 @@ typedef struct {
   int use_graphs;       /* 1: capture each GMRES cycle in a CUDA graph */
   int coarse;           /* 1: add the rigid-body coarse correction to the preconditioner */
   int coarse_max;       /* bound on the coarse unknowns (16..4096): sets the aggregate size */
+  int reorth;           /* 1 (default): classical Gram-Schmidt with a second, re-orthogonalising
+                           pass; FP32 cycles lose orthogonality without it */
 } hf_solver_opts;
 
 /* Report of one Newton iteration (Sec. 3: convergence on the Euclidean norms

@@ -35,7 +35,7 @@ class hf_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int),
                 ("rtol", C.c_double), ("inner_rtol", C.c_double), ("jacobi_block", C.c_int),
                 ("fluid_scaling", C.c_int), ("newton_tol", C.c_double), ("use_graphs", C.c_int),
-                ("coarse", C.c_int), ("coarse_max", C.c_int)]
+                ("coarse", C.c_int), ("coarse_max", C.c_int), ("reorth", C.c_int)]
 
 
 class hf_newton_report(C.Structure):

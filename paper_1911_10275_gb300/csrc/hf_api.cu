@@ -471,7 +471,7 @@ extern "C" {
 void hf_default_solver_opts(hf_solver_opts* o) {
   if (!o) return;
   o->precision = HF_PREC_FP64;
-  o->restart = 30;
+  o->restart = 60;
   o->max_iters = 3000;
   o->rtol = 1e-12;
   o->inner_rtol = 1e-4;
@@ -481,6 +481,7 @@ void hf_default_solver_opts(hf_solver_opts* o) {
   o->use_graphs = 0;
   o->coarse = 1;
   o->coarse_max = 2048;
+  o->reorth = 1;
 }
 
 const char* hf_last_error(const hf_mesh* h) { return h ? h->err.c_str() : "null handle"; }
@@ -824,7 +825,7 @@ hf_status hf_set_solver(hf_mesh* h, const hf_solver_opts* o) {
   HF_GUARD(h);
   if (!o || (o->precision != HF_PREC_FP64 && o->precision != HF_PREC_MIXED) || o->restart < 1 || o->restart > GM_MAX ||
       o->max_iters < 0 || !(o->rtol > 0) || !(o->inner_rtol > 0) || o->jacobi_block < 1 || o->coarse < 0 ||
-      o->coarse > 1 || o->coarse_max < 16 || o->coarse_max > 4096)
+      o->coarse > 1 || o->coarse_max < 16 || o->coarse_max > 4096 || o->reorth < 0 || o->reorth > 1)
     return set_error(h, HF_ERR_INVALID_ARG, "solver options out of range");
   bool regroup = std::min(256, o->jacobi_block) != h->G;
   bool rescale = o->fluid_scaling != h->opts.fluid_scaling;
@@ -1324,7 +1325,9 @@ hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, const hf_solver_opt
   const int jacobi_block = o.jacobi_block;
   // the bases are sized for the longest cycle the handle has been given: the
   // default at creation, then this one
-  const long long mres = std::max(1, std::min(GM_MAX, std::max(o.restart, 30)));
+  hf_solver_opts dflt;
+  hf_default_solver_opts(&dflt);
+  const long long mres = std::max(1, std::min(GM_MAX, std::max(o.restart, dflt.restart)));
   const long long dim = desc->dim, ne = desc->n_elems, nf = desc->n_faces, nn = desc->n_nodes;
   const long long nen = dim == 2 ? 6 : 10, ned = nen * dim, nfn = dim == 2 ? 3 : 6, nfr = nfn * dim, nsl = dim + 1;
   const long long nld = 4 * nfn * nfn + 3 * nfn, lus = ned * ned + nsl * ned * nfr;

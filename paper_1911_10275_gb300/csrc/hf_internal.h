@@ -64,6 +64,7 @@ struct GmresState {
   int iters;
   int pad;
   double g[GM_LD];
+  double h2[GM_LD];      // second Gram-Schmidt pass coefficients
   double cs[GM_MAX], sn[GM_MAX];
   double y[GM_MAX];
   double H[GM_LD * GM_MAX];  // Hessenberg, rotated in place (column-major, ld GM_LD)

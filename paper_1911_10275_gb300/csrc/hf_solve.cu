@@ -811,7 +811,7 @@ __device__ double block_sum_partials(const double* partial, int n, int stride, i
 // re-read per chunk, from L2)
 template <typename T>
 __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long ldv, int j, const T* __restrict__ w,
-                                             long long n, double* partial, int* counter, GmresState* gs) {
+                                             long long n, double* partial, int* counter, GmresState* gs, double* hout) {
   if (gs->done) return;
   __shared__ double sm[RB / 32][32];
   __shared__ bool last;
@@ -883,7 +883,7 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
       if (threadIdx.x < 32 && q0 + (int)threadIdx.x < ncols) {
         double tot = 0.0;
         for (int g2 = 0; g2 < RB / 32; ++g2) tot += red[g2][threadIdx.x];
-        gs->H[j * GM_LD + q0 + threadIdx.x] = tot;
+        hout[q0 + threadIdx.x] = tot;
       }
       __syncthreads();
     }
@@ -894,11 +894,14 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
 // w -= V h; ||w||; Givens update of column j; convergence test
 template <typename T>
 __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
-                                             double* partial, int* counter, GmresState* gs, int mrest) {
+                                             double* partial, int* counter, GmresState* gs, int mrest,
+                                             const double* hsrc, int accumulate) {
+  // w -= V hsrc; with accumulate (second Gram-Schmidt pass, hsrc = gs->h2)
+  // the coefficients are added to column j of H before the Givens update
   if (gs->done) return;
   __shared__ T h[GM_MAX];
   const int ncols = j + 1;
-  for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) h[c] = c < ncols ? (T)gs->H[j * GM_LD + c] : (T)0;
+  for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) h[c] = c < ncols ? (T)hsrc[c] : (T)0;
   __syncthreads();
   T acc_t = (T)0;
   using VT = typename Vec<T>::type;
@@ -923,6 +926,8 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
   if (threadIdx.x == 0) {
     double nrm = sqrt(nrm2);
     double* hc = gs->H + j * GM_LD;
+    if (accumulate)
+      for (int i = 0; i <= j; ++i) hc[i] += hsrc[i];
     for (int i = 0; i < j; ++i) {
       double a = hc[i], b = hc[i + 1];
       hc[i] = gs->cs[i] * a + gs->sn[i] * b;
@@ -942,6 +947,32 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
     gs->jlast = j + 1;
     if (fabs(gs->g[j + 1]) <= gs->tol_abs || j + 1 >= mrest || !(nrm > 0.0) || !isfinite(nrm)) gs->done = 1;
     *counter = 0;
+  }
+}
+
+// first pass of classical Gram-Schmidt with reorthogonalisation: w -= V H[:, j]
+template <typename T>
+__global__ void __launch_bounds__(RB) k_orth_sub(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
+                                                 const GmresState* gs) {
+  if (gs->done) return;
+  __shared__ T h[GM_MAX];
+  const int ncols = j + 1;
+  for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) h[c] = c < ncols ? (T)gs->H[j * GM_LD + c] : (T)0;
+  __syncthreads();
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  for (long long iv = tid; iv < nv; iv += stride) {
+    VT ww = reinterpret_cast<const VT*>(w)[iv];
+#pragma unroll 8
+    for (int c = 0; c < ncols; ++c) Vec<T>::axpy(ww, h[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
+    reinterpret_cast<VT*>(w)[iv] = ww;
+  }
+  for (long long i = nv * VN + tid; i < n; i += stride) {
+    T ww = w[i];
+    for (int c = 0; c < ncols; ++c) ww -= h[c] * V[c * ldv + i];
+    w[i] = ww;
   }
 }
 
@@ -1370,8 +1401,14 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
     spmv<T, DIM, 0>(h, dg, off, K.z, K.w, done);
     prof_end(h);
     prof_begin(h, PK_ORTH);
-    { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs); }
-    { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest); }
+    { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->H + j * GM_LD); }
+    if (h->opts.reorth) {
+      { note_launch(); k_orth_sub<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, gs); }
+      { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->h2); }
+      { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->h2, 1); }
+    } else {
+      { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->H + j * GM_LD, 0); }
+    }
     { note_launch(); k_scale_into<T><<<rb, RB, 0, h->stream>>>(K.w, K.V + (long long)(j + 1) * K.ldv, N, &gs->inv_h, done); }
     prof_end(h);
   }

@@ -103,6 +103,10 @@ def test_coarse_correction_is_the_galerkin_projection(make):
     rng = np.random.default_rng(11)
     r = np.zeros(o.N)
     r[:nu] = rng.standard_normal(nu)
+    # Dirichlet rows are identity rows whose columns stay in J: an O(1) entry
+    # there gives O(1) preconditioner output in its element, and the O(1e-11)
+    # coarse part would drown in its rounding.  Newton residuals vanish there.
+    r[m.dir_dof] = 0.0
     z2 = g.hf_apply_preconditioner(r)
     g.hf_set_solver(precision="fp64", jacobi_block=8, coarse=0, coarse_max=64, rtol=1e-13, max_iters=20000)
     z1 = g.hf_apply_preconditioner(r)
@@ -111,7 +115,7 @@ def test_coarse_correction_is_the_galerkin_projection(make):
     A0 = Phi.T @ (Juu @ Phi)
     want = Phi @ np.linalg.solve(A0, Phi.T @ r[:nu])
     got = (z2 - z1)[:nu]
-    assert np.abs(got - want).max() <= 1e-8 * np.abs(want).max()
+    assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
 
 
 def test_coarse_level_cuts_gmres_iterations():
@@ -129,5 +133,8 @@ def test_coarse_level_cuts_gmres_iterations():
         g.close()
     assert all(r["lin_converged"] for r in reps)
     assert reps[1]["gmres_iters"] < reps[0]["gmres_iters"]
+    # a relative residual of 1e-8 bounds the error only through the condition
+    # number of J (force, flux and identity rows together): two solves that
+    # both meet it agree to ~1e-5 in the displacements here
     U0, U1 = states[0][0], states[1][0]
-    assert np.abs(U1 - U0).max() <= 1e-6 * np.abs(U0).max()
+    assert np.abs(U1 - U0).max() <= 1e-4 * np.abs(U0).max()
