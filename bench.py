@@ -424,11 +424,15 @@ def oracle_baseline(wl, budget_s):
 
 
 def _solver_for_requests(args, tuner=None):
-    base = {"precision": args.precision, "rtol": 1e-8, "inner_rtol": 1e-3, "max_iters": 20000, "newton_tol": 1e-8,
-            "use_graphs": 1, "jacobi_block": args.jacobi_block, "restart": args.restart}
+    base = {"precision": args.precision, "rtol": 1e-8, "inner_rtol": 1e-3, "max_iters": args.request_max_iters,
+            "newton_tol": 1e-8, "use_graphs": 1, "jacobi_block": args.jacobi_block, "restart": args.restart,
+            "reorth": args.reorth, "coarse": args.coarse}
     if tuner is None:
         return lambda wl: dict(base)
-    return lambda wl: {**tuner.solver_for(wl, args.precision), "max_iters": 20000}
+    return lambda wl: {**tuner.solver_for(wl, args.precision), "max_iters": args.request_max_iters}
+
+
+REQUEST_STEP = {"newton_max": 8, "criterion_rounds": 4, "max_cutbacks": 4}
 
 
 def serving_run(args, count, rate, slots, seed=191110275, warm=True):
@@ -447,8 +451,8 @@ def serving_run(args, count, rate, slots, seed=191110275, warm=True):
     rt = HFRuntime(slots=slots, hbm_budget_bytes=budget)
     solver_for = _solver_for_requests(args)
     if warm:  # one small request first, so that module loading is not in the first latency
-        run_stream(rt, [0.0], reqs[:1], 1, solver_for)
-    recs = run_stream(rt, arrivals, reqs, args.serve_steps, solver_for)
+        run_stream(rt, [0.0], reqs[:1], 1, solver_for, step=REQUEST_STEP)
+    recs = run_stream(rt, arrivals, reqs, args.serve_steps, solver_for, step=REQUEST_STEP)
     st = rt.stats()
     rt.close()
     summ = latency_summary(recs)
@@ -463,6 +467,14 @@ def serving_run(args, count, rate, slots, seed=191110275, warm=True):
     return summ, recs
 
 
+def _log_records(recs):
+    for r in recs:
+        print(f"{r['name']:26s} status={r['status']} unknowns={r['n_u'] + r['n_p']} steps={r['steps_done']} "
+              f"newton={r['newton_iters']} gmres={r['gmres_iters']} cutbacks={r['cutbacks']} "
+              f"latency={r['latency']:.2f}s queue={r['queue'] if r['queue'] is None else round(r['queue'], 2)}",
+              file=sys.stderr)
+
+
 def run_serve(args):
     """The serving configuration: a Poisson stream of solve requests (half
     2D KGD, half 3D penny), admitted by HBM budget into `slots` concurrent
@@ -473,6 +485,8 @@ def run_serve(args):
     sampler.start()
     summ, recs = serving_run(args, args.serve_requests, args.serve_rate, args.slots)
     clocks = sampler.stop()
+    if args.verbose:
+        _log_records(recs)
     out = {"metric": "serving latency p99 (ms) under a Poisson request stream", "value": summ.get("p99_ms"),
            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "mode": "serve", "data": "synthetic",
            "dtype": "f32-inner/f64-refinement" if args.precision == "mixed" else "f64",
@@ -507,9 +521,11 @@ def run_sweep(args):
     sampler = ClockSampler(0)
     sampler.start()
     t0 = time.perf_counter()
-    recs = run_stream(rt, [0.0] * len(wls), wls, args.sweep_steps, solver_for)
+    recs = run_stream(rt, [0.0] * len(wls), wls, args.sweep_steps, solver_for, step=REQUEST_STEP)
     span = time.perf_counter() - t0
     clocks = sampler.stop()
+    if args.verbose:
+        _log_records(recs)
     st = rt.stats()
     rt.close()
     summ = latency_summary(recs)
@@ -570,6 +586,8 @@ def main():
     ap.add_argument("--sweep-count", dest="sweep_count", type=int, default=256)
     ap.add_argument("--sweep-steps", dest="sweep_steps", type=int, default=10)
     ap.add_argument("--autotune", type=int, default=1)
+    ap.add_argument("--verbose", type=int, default=0)
+    ap.add_argument("--request-max-iters", dest="request_max_iters", type=int, default=3000)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

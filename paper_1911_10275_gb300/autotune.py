@@ -11,7 +11,7 @@ from __future__ import annotations
 import math
 import time
 
-CANDIDATES = tuple((G, m) for G in (8, 16, 32, 64) for m in (20, 30))
+CANDIDATES = tuple((G, m) for G in (8, 16, 32) for m in (60, 90))
 
 
 def size_class(wl, precision):
@@ -50,7 +50,7 @@ class Tuner:
 
     def __init__(self, base=None, candidates=CANDIDATES, newton_iters=2):
         self.base = dict(base or {"rtol": 1e-8, "inner_rtol": 1e-3, "max_iters": 3000, "newton_tol": 1e-8,
-                                  "use_graphs": 1})
+                                  "use_graphs": 1, "reorth": 1, "coarse": 1})
         self.candidates = tuple(candidates)
         self.newton_iters = newton_iters
         self.best = {}

@@ -233,19 +233,21 @@ __global__ void k_coarse_to_f(const double* __restrict__ a, float* __restrict__ 
 }
 
 // c = Phi^T r, one block per aggregate (fixed-order tree reduction)
+constexpr int RESTRICT_THREADS = 512;
+
 template <typename T, int DIM>
-__global__ void __launch_bounds__(128) k_coarse_restrict(DevMesh m, int A, const T* __restrict__ rc,
-                                                         const T* __restrict__ r, T* __restrict__ cc,
-                                                         const int* skip) {
-  constexpr int NED = Shape<DIM>::ned, NM = n_modes<DIM>();
-  __shared__ T red[NM][128];
+__global__ void __launch_bounds__(RESTRICT_THREADS) k_coarse_restrict(DevMesh m, int A, const T* __restrict__ rc,
+                                                                      const T* __restrict__ r, T* __restrict__ cc,
+                                                                      const int* skip) {
+  constexpr int NED = Shape<DIM>::ned, NM = n_modes<DIM>(), NT = RESTRICT_THREADS;
+  __shared__ T red[NM][NT];
   if (skip && *skip) return;
   const int g = blockIdx.x, t = threadIdx.x;
   const long long i0 = (long long)g * A * NED, i1 = (long long)min(m.ne, (g + 1) * A) * NED;
   T s[NM];
 #pragma unroll
   for (int k = 0; k < NM; ++k) s[k] = (T)0;
-  for (long long i = i0 + t; i < i1; i += 128) {
+  for (long long i = i0 + t; i < i1; i += NT) {
     const int e = (int)(i / NED), c = (int)(i % NED);
     if ((m.dirmask[e] >> c) & 1u) continue;
     T X[DIM];
@@ -259,7 +261,7 @@ __global__ void __launch_bounds__(128) k_coarse_restrict(DevMesh m, int A, const
 #pragma unroll
   for (int k = 0; k < NM; ++k) red[k][t] = s[k];
   __syncthreads();
-  for (int o = 64; o > 0; o >>= 1) {
+  for (int o = NT / 2; o > 0; o >>= 1) {
     if (t < o)
 #pragma unroll
       for (int k = 0; k < NM; ++k) red[k][t] += red[k][t + o];
@@ -276,8 +278,17 @@ __global__ void k_coarse_gemv(const T* __restrict__ Ainv, int nc, const T* __res
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= nc) return;
   const T* a = Ainv + (long long)row * nc;
-  T s = (T)0;
-  for (int j = lane; j < nc; j += 32) s += a[j] * cc[j];
+  // four independent partial sums keep four loads in flight per lane
+  T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+  int j = lane;
+  for (; j + 96 < nc; j += 128) {
+    s0 += a[j] * cc[j];
+    s1 += a[j + 32] * cc[j + 32];
+    s2 += a[j + 64] * cc[j + 64];
+    s3 += a[j + 96] * cc[j + 96];
+  }
+  for (; j < nc; j += 32) s0 += a[j] * cc[j];
+  T s = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) cy[row] = s;
@@ -288,20 +299,28 @@ template <typename T, int DIM>
 __global__ void k_coarse_prolong(DevMesh m, int A, const T* __restrict__ rc, const T* __restrict__ cy, T* z,
                                  const int* skip) {
   constexpr int NED = Shape<DIM>::ned, NM = n_modes<DIM>();
+  // one thread per element node: its coordinates are read once for its DIM unknowns
   if (skip && *skip) return;
-  long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= (long long)m.ne * NED) return;
-  const int e = (int)(i / NED), c = (int)(i % NED);
-  if ((m.dirmask[e] >> c) & 1u) return;
+  constexpr int NEN = Shape<DIM>::nen;
+  long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (long long)m.ne * NEN) return;
+  const int e = (int)(q / NEN), a = (int)(q % NEN);
+  const unsigned dm = m.dirmask[e];
+  const long long nb = (long long)e * NED + a * DIM;
   T X[DIM];
-  const long long nb = (long long)e * NED + (c / DIM) * DIM;
 #pragma unroll
   for (int k = 0; k < DIM; ++k) X[k] = rc[nb + k];
-  const T* y = cy + (long long)(e / A) * NM;
-  T s = (T)0;
+  T y[NM];
 #pragma unroll
-  for (int k = 0; k < NM; ++k) s += rbm<DIM>(k, c % DIM, X) * y[k];
-  z[i] += s;
+  for (int k = 0; k < NM; ++k) y[k] = cy[(long long)(e / A) * NM + k];
+#pragma unroll
+  for (int comp = 0; comp < DIM; ++comp) {
+    if ((dm >> (a * DIM + comp)) & 1u) continue;
+    T s = (T)0;
+#pragma unroll
+    for (int k = 0; k < NM; ++k) s += rbm<DIM>(k, comp, X) * y[k];
+    z[nb + comp] += s;
+  }
 }
 
 // ---------------------------------------------------------------- host side
@@ -419,13 +438,14 @@ template <> const float* coarse_coords<float>(const hf_mesh* h) { return h->rc32
 template <typename T, int DIM>
 void coarse_pre(hf_mesh* h, const Krylov<T>& K, const T* rin, const int* skip) {
   note_launch();
-  k_coarse_restrict<T, DIM><<<h->nagg, 128, 0, h->stream>>>(h->d, h->agg_size, coarse_coords<T>(h), rin, K.cc, skip);
+  k_coarse_restrict<T, DIM><<<h->nagg, RESTRICT_THREADS, 0, h->stream>>>(h->d, h->agg_size, coarse_coords<T>(h), rin,
+                                                                           K.cc, skip);
   note_launch();
   k_coarse_gemv<T><<<(h->nc + 7) / 8, 256, 0, h->stream>>>(coarse_inverse<T>(h), h->nc, K.cc, K.cy, skip);
 }
 
 template <typename T, int DIM> void coarse_post(hf_mesh* h, const Krylov<T>& K, T* z, const int* skip) {
-  const long long n = h->ne * (long long)Shape<DIM>::ned;
+  const long long n = h->ne * (long long)Shape<DIM>::nen;
   note_launch();
   k_coarse_prolong<T, DIM><<<(unsigned)((n + 255) / 256), 256, 0, h->stream>>>(h->d, h->agg_size,
                                                                                coarse_coords<T>(h), K.cy, z, skip);
