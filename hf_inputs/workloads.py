@@ -90,6 +90,9 @@ def c3_penny():
 
 # ---------------------------------------------------------------- many instances
 def _even(x, lo, hi):
+    """Even integer nearest x within [lo, hi] (bounds rounded inwards to even)."""
+    lo = lo + (lo % 2)
+    hi = hi - (hi % 2)
     n = int(round(x / 2.0)) * 2
     return max(lo, min(hi, n))
 
@@ -106,11 +109,39 @@ def sample_parameters(rng):
             "mu": _log_uniform(rng, 1e-3, 1.0), "Q0": _log_uniform(rng, 1e-4, 1e-2)}
 
 
+def toughness_consistent(wl: Workload, sigma_c_max=1e6, zone_elems=4.0) -> Workload:
+    """The same instance with a seed and a cohesive strength that its
+    parameters can support, for draws over wide parameter ranges:
+
+    * the seed pressure p0 is the one at which the seed crack (half-length or
+      radius a) is at its toughness: K_I = K_Ic with K_I = p sqrt(pi a) for the
+      plane-strain crack and 2 p sqrt(a / pi) for the penny crack;
+    * the seed opening is the static elastic opening of that pressure at the
+      centre: 4 p0 a / E' in plane strain, 8 p0 a / (pi E') for the penny
+      (E' = E / (1 - nu^2));
+    * sigma_c is lowered below sigma_c_max where needed so that the cohesive
+      length E' G_c / sigma_c^2 = K_Ic^2 / sigma_c^2 spans zone_elems elements.
+    """
+    m = wl.mesh
+    h = m.length / m.n
+    a = wl.seed_radius
+    Ep = wl.E / (1.0 - wl.nu ** 2)
+    if m.dim == 2:
+        p0 = wl.K_Ic / math.sqrt(math.pi * a)
+        w0 = 4.0 * p0 * a / Ep
+    else:
+        p0 = wl.K_Ic * math.sqrt(math.pi) / (2.0 * math.sqrt(a))
+        w0 = 8.0 * p0 * a / (math.pi * Ep)
+    sigma_c = min(sigma_c_max, wl.K_Ic / math.sqrt(zone_elems * h))
+    return dataclasses.replace(wl, p0=p0, w0=w0, sigma_c=sigma_c)
+
+
 def sweep_instances(count=256, seed=191110275, ne_range=(1000, 50000), steps=10, mesh_cache=None):
     """Batched 2D KGD sweep: `count` independent plane-strain instances with
     the draws of batch_instances (element count, E, K_Ic, mu, Q0 log-uniform),
-    nu = 0.2, sigma_c = 1 MPa, crack on the midline.  Meshes of equal n are
-    shared through mesh_cache (a dict)."""
+    nu = 0.2, sigma_c = 1 MPa at most, crack on the midline, seed and sigma_c
+    from toughness_consistent.  Meshes of equal n are shared through
+    mesh_cache (a dict)."""
     cache = {} if mesh_cache is None else mesh_cache
     out = []
     for i, d in enumerate(batch_instances(count, seed, ne_range)):
@@ -119,8 +150,9 @@ def sweep_instances(count=256, seed=191110275, ne_range=(1000, 50000), steps=10,
         if key not in cache:
             cache[key] = square_p2(n, 100.0, crackable="midline")
         h = 100.0 / n
-        out.append(Workload(f"sweep{i}_kgd2d_n{n}", cache[key], d["E"], 0.2, d["K_Ic"], 1e6, d["mu"], d["Q0"], 1.0,
-                            steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6))
+        out.append(toughness_consistent(
+            Workload(f"sweep{i}_kgd2d_n{n}", cache[key], d["E"], 0.2, d["K_Ic"], 1e6, d["mu"], d["Q0"], 1.0,
+                     steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6)))
     return out
 
 
@@ -131,9 +163,8 @@ def serving_requests(count=2000, rate=200.0, seed=191110275, kgd_n=(50, 316), pe
     n in kgd_n), half penny-shaped (n^3 cubes of six P2 tetrahedra, n in
     penny_n, crack plane z = 0), parameters from sample_parameters (nu = 0.2
     for KGD, 0.25 for the penny), `steps` time steps each from the seed
-    state.  sigma_c is 1 MPa for KGD and 0.3 MPa for the penny (a cohesive
-    length spanning several tetrahedra, as in the penny benchmark).  Returns
-    (arrival times in s, workloads)."""
+    state; seed and sigma_c (at most 1 MPa for KGD, 0.3 MPa for the penny)
+    from toughness_consistent.  Returns (arrival times in s, workloads)."""
     rng = np.random.default_rng(seed)
     cache = {} if mesh_cache is None else mesh_cache
     t = np.cumsum(rng.exponential(1.0 / rate, size=count))
@@ -146,14 +177,16 @@ def serving_requests(count=2000, rate=200.0, seed=191110275, kgd_n=(50, 316), pe
             if key not in cache:
                 cache[key] = square_p2(n, 100.0, crackable="midline")
             h = 100.0 / n
-            out.append(Workload(f"req{i}_kgd2d_n{n}", cache[key], prm["E"], 0.2, prm["K_Ic"], 1e6, prm["mu"],
-                                prm["Q0"], 1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6))
+            out.append(toughness_consistent(
+                Workload(f"req{i}_kgd2d_n{n}", cache[key], prm["E"], 0.2, prm["K_Ic"], 1e6, prm["mu"], prm["Q0"], 1.0,
+                         steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6)))
         else:
             n = _even(math.exp(rng.uniform(math.log(penny_n[0]), math.log(penny_n[1]))), penny_n[0] + 1, penny_n[1])
             key = ("penny", n)
             if key not in cache:
                 cache[key] = cube_p2(n, 50.0, crackable="plane")
             h = 50.0 / n
-            out.append(Workload(f"req{i}_penny3d_n{n}", cache[key], prm["E"], 0.25, prm["K_Ic"], 0.3e6, prm["mu"],
-                                prm["Q0"], 1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=2e-3, p0=1e6))
+            out.append(toughness_consistent(
+                Workload(f"req{i}_penny3d_n{n}", cache[key], prm["E"], 0.25, prm["K_Ic"], 0.3e6, prm["mu"], prm["Q0"],
+                         1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=2e-3, p0=1e6), sigma_c_max=0.3e6))
     return t, out

@@ -245,7 +245,8 @@ hf_status hf_increment_norms_noalloc(const double* d_dx, const double* d_x, int6
 typedef struct {
   int newton_max;        /* Newton iterations per attempt before the step is cut (default 8) */
   int criterion_rounds;  /* criterion / Newton-again rounds per sub-step (default 4) */
-  int max_cutbacks;      /* halvings of the sub-step before the call gives up (default 10) */
+  int max_cutbacks;      /* consecutive failed attempts (each halving the sub-step) before the call
+                           gives up (default 10); at most 256 attempts in all */
 } hf_step_opts;
 
 typedef struct {
@@ -270,8 +271,9 @@ void hf_default_step_opts(hf_step_opts* o);
  * non-finite is undone from a device copy of the start-of-step state and
  * retried with half the sub-step; after a success the sub-step grows by 1.5
  * up to dt, until t + dt is reached.  dt itself is left unchanged.  Errors:
- * HF_ERR_NOT_CONVERGED after max_cutbacks halvings (state = the last accepted
- * sub-step), any CUDA or state error as returned by the calls above. */
+ * HF_ERR_NOT_CONVERGED after max_cutbacks consecutive failures or 256
+ * attempts (state = the last accepted sub-step), any CUDA or state error as
+ * returned by the calls above. */
 hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* rep);
 
 /* Aggregate of each element (caller's element order) in the coarse level of

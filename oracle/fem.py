@@ -594,11 +594,15 @@ class Oracle:
         R, J = self.assemble()
         d = self.solve_linear(J, -R) if solve is None else solve(J, -R)
         dU, dP = d[: self.Nu], d[self.Nu:]
+        P_old = self.P
         self.U = self.U + dU
         self.P = self.P + dP
         if self.prm.cutoff_on:
             act = self.active_pdofs()
             self.P[act] = np.maximum(self.P[act], self.prm.p_vapor)
+            # the increment of the nodal pressure array is the change applied,
+            # cut-off included
+            dP = self.P - P_old
         du = np.linalg.norm(dU) / max(np.linalg.norm(self.U), 1e-300)
         dp = np.linalg.norm(dP) / max(np.linalg.norm(self.P), 1e-300)
         return dict(du_rel=du, dp_rel=dp, res_norm=float(np.linalg.norm(R)),

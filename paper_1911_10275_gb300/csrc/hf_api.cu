@@ -1033,6 +1033,9 @@ static hf_status snap_restore(hf_mesh* h) {
   return check_cuda(h, cudaGetLastError(), "restore");
 }
 
+// attempts (accepted sub-steps and failures) one hf_advance_step may take
+constexpr int HF_STEP_MAX_ATTEMPTS = 256;
+
 // the time-step length enters the facet records and the pressure rows, both
 // baked into captured GMRES cycles
 static void set_dt(hf_mesh* h, double dt) {
@@ -1197,7 +1200,8 @@ hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* 
   hf_step_report r{};
   const double dt0 = h->dt, target = h->t + dt0;
   double sub = dt0;
-  int cuts = 0;
+  int cuts = 0;         // consecutive failed attempts
+  int attempts = 0;
   hf_status s = snap_save(h);
   if (s) return s;
   while (target - h->t > 1e-12 * dt0) {
@@ -1237,6 +1241,7 @@ hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* 
       }
       if (it >= o.newton_max) break;
     }
+    ++attempts;
     if (ok) {
       int64_t nb = 0;
       if ((s = hf_accept_step(h, &nb))) {
@@ -1245,11 +1250,12 @@ hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* 
       }
       r.new_beta += nb;
       ++r.substeps;
+      cuts = 0;
       if ((s = snap_save(h))) return s;
       sub = std::min(dt0, 1.5 * sub);
     } else {
       if ((s = snap_restore(h))) return s;
-      if (++cuts > o.max_cutbacks) {
+      if (++cuts > o.max_cutbacks || attempts >= HF_STEP_MAX_ATTEMPTS) {
         set_dt(h, dt0);
         if (rep) *rep = r;
         return set_error(h, HF_ERR_NOT_CONVERGED, "time step not converged after the allowed cutbacks");

@@ -1108,11 +1108,14 @@ __global__ void __launch_bounds__(RB) k_newton_update(DevMesh m, double* X, cons
   double a[4] = {0, 0, 0, 0};
   long long stride = (long long)gridDim.x * blockDim.x;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < m.N; i += stride) {
-    double d = Dx[i];
-    double x = X[i] + d;
+    // the increment measured is the change applied to the state, after the
+    // pressure cut-off (a clipped pressure that stays clipped has converged)
+    const double x0 = X[i];
+    double x = x0 + Dx[i];
     bool isp = i >= m.nu;
     if (isp && m.cutoff && m.p_active[i - m.nu] && x < m.p_v) x = m.p_v;
     X[i] = x;
+    const double d = x - x0;
     a[isp ? 2 : 0] += d * d;
     a[isp ? 3 : 1] += x * x;
   }

@@ -57,7 +57,8 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
     switched facets (at most rounds_max rounds), end of step; an attempt that
     does not converge within newton_max iterations (or turns non-finite) is
     undone and retried with half the sub-step, which grows back by 1.5 after
-    each accepted sub-step until t + dt is reached."""
+    each accepted sub-step until t + dt is reached; at most max_cutbacks
+    failures in a row, 256 attempts in all."""
     dt0 = o.prm.dt
     target = o.t + dt0
     sub = dt0
@@ -67,6 +68,7 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
         return (o.U.copy(), o.P.copy(), o.alpha.copy(), o.beta.copy(), o.w_old.copy(), o.t)
 
     saved = snap()
+    cuts = attempts = 0
     while target - o.t > 1e-12 * dt0:
         sub = min(sub, target - o.t)
         o.prm.dt = sub
@@ -87,15 +89,18 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
                 continue
             if it >= newton_max:
                 break
+        attempts += 1
         if ok:
             o.accept_step()
             rep["substeps"] += 1
+            cuts = 0
             saved = snap()
             sub = min(dt0, 1.5 * sub)
         else:
             o.set_state(*saved)
+            cuts += 1
+            assert cuts <= max_cutbacks and attempts < 256
             rep["cutbacks"] += 1
-            assert rep["cutbacks"] <= max_cutbacks
             sub *= 0.5
     o.t = target
     o.prm.dt = dt0
