@@ -117,6 +117,7 @@ typedef struct {
   int refinements;      /* mixed mode: outer refinement steps */
   int converged;        /* du_rel <= tol && dp_rel <= tol */
   int lin_converged;    /* lin_res <= rtol */
+  int fp64_fallback;    /* mixed mode: FP32 sweeps stalled, the solve finished in FP64 */
 } hf_newton_report;
 
 void hf_default_solver_opts(hf_solver_opts* o);
@@ -243,7 +244,9 @@ hf_status hf_increment_norms_noalloc(const double* d_dx, const double* d_x, int6
 
 /* Options of hf_advance_step. */
 typedef struct {
-  int newton_max;        /* Newton iterations per attempt before the step is cut (default 8) */
+  int newton_max;        /* Newton iterations per attempt before the step is cut (default 8); past
+                           it, iterations go on while the increments at least halve each time, up
+                           to 4 newton_max */
   int criterion_rounds;  /* criterion / Newton-again rounds per sub-step (default 4) */
   int max_cutbacks;      /* consecutive failed attempts (each halving the sub-step) before the call
                            gives up (default 10); at most 256 attempts in all */

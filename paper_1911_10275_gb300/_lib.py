@@ -41,7 +41,7 @@ class hf_solver_opts(C.Structure):
 class hf_newton_report(C.Structure):
     _fields_ = [("du_rel", C.c_double), ("dp_rel", C.c_double), ("res_norm", C.c_double),
                 ("lin_res", C.c_double), ("gmres_iters", C.c_int), ("refinements", C.c_int),
-                ("converged", C.c_int), ("lin_converged", C.c_int)]
+                ("converged", C.c_int), ("lin_converged", C.c_int), ("fp64_fallback", C.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

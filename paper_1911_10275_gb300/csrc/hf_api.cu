@@ -1209,6 +1209,7 @@ hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* 
     set_dt(h, sub);
     bool ok = false;
     int rounds = 0, it = 0;
+    double prev_inc = HUGE_VAL;  // largest relative increment of the previous iteration
     for (;;) {  // Newton to convergence, then the criterion; Newton again if it switched facets
       hf_newton_report nr{};
       s = hf_newton_step(h, &nr);
@@ -1237,9 +1238,14 @@ hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* 
           break;
         }
         it = 0;
+        prev_inc = HUGE_VAL;
         continue;
       }
-      if (it >= o.newton_max) break;
+      // past newton_max, keep going only while the increments still at least
+      // halve every iteration (linear convergence), up to 4 newton_max
+      const double inc = std::max(nr.du_rel, nr.dp_rel);
+      if (it >= o.newton_max && (it >= 4 * o.newton_max || !(inc <= 0.5 * prev_inc))) break;
+      prev_inc = inc;
     }
     ++attempts;
     if (ok) {

@@ -23,6 +23,7 @@
 #include <mutex>
 #include <algorithm>
 #include <cmath>
+#include <numeric>
 #include <cstdio>
 
 #include "hf_internal.h"
@@ -1504,32 +1505,16 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
     }
     return HF_OK;
   }
-  if (o.precision == HF_PREC_FP64) {
-    Krylov<double>& K = h->K64;
-    { note_launch(); k_fill<double><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0); }
-    for (;;) {
-      spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, K.x, K.w, nullptr);
-      { note_launch(); k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, K.w, K.V, N, h->d_partial, cnt, h->d_gs, tol); }
-      { note_launch(); k_scale_into<double><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
-      CycleInfo ci;
-      cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
-      if ((st = read_gs(h, &ci))) break;
-      rnorm = ci.beta;
-      if (!std::isfinite(rnorm)) {
-        st = set_error(h, HF_ERR_NONFINITE, "GMRES residual is not finite");
-        break;
-      }
-      if (rnorm <= tol || total >= o.max_iters) break;
-      if ((st = run_cycle<double, DIM>(h, K, h->J64.dg, h->J64.off, mrest, &h->graph64, &h->gev64))) break;
-      if ((st = read_gs(h, &ci))) break;
-      if (o.use_graphs) prof_flush_graph(h, h->gev64, ci.iters);
-      total += ci.iters;
-    }
-    cudaMemcpyAsync(x, K.x, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
-  } else {
+  // FP32 refinement sweeps first in mixed precision; when two sweeps in a
+  // row fail to halve the FP64 residual (an FP32 operator too coarse for this
+  // system), the solve goes on in FP64 from the current iterate
+  bool use64 = o.precision == HF_PREC_FP64, fell_back = false;
+  if (!use64) {
     Krylov<float>& K = h->K32;
     if (!h->j32_valid) convert_j32(h);
     double* r = h->r64;
+    int poor = 0;
+    double prev = bnorm;
     cudaMemcpyAsync(r, b, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
     for (;;) {
       { note_launch(); k_norm2<double><<<rb, RB, 0, h->stream>>>(r, N, h->d_partial, cnt, h->d_red); }
@@ -1542,6 +1527,14 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
         break;
       }
       if (rnorm <= tol || total >= o.max_iters) break;
+      if (refinements > 0) {
+        poor = rnorm > 0.5 * prev ? poor + 1 : 0;
+        if (poor >= 2) {
+          use64 = fell_back = true;
+          break;
+        }
+      }
+      prev = rnorm;
       { note_launch(); k_demote_scaled<<<rb, RB, 0, h->stream>>>(r, K.b, N, h->d_red); }
       { note_launch(); k_fill<float><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0f); }
       { note_launch(); k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs, o.inner_rtol); }
@@ -1561,9 +1554,42 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
       if (ci.iters == 0) break;
     }
   }
+  if (use64 && !st) {
+    Krylov<double>& K = h->K64;
+    if (fell_back) {
+      std::vector<int> all(h->d.nsd);
+      std::iota(all.begin(), all.end(), 0);
+      if (DIM == 2) factor_impl<double, 2>(h, all, h->K64.lu, h->K64.sinv);
+      else factor_impl<double, 3>(h, all, h->K64.lu, h->K64.sinv);
+      cudaMemcpyAsync(K.x, x, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+    } else {
+      note_launch();
+      k_fill<double><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0);
+    }
+    for (;;) {
+      spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, K.x, K.w, nullptr);
+      { note_launch(); k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, K.w, K.V, N, h->d_partial, cnt, h->d_gs, tol); }
+      { note_launch(); k_scale_into<double><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
+      CycleInfo ci;
+      cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
+      if ((st = read_gs(h, &ci))) break;
+      rnorm = ci.beta;
+      if (!std::isfinite(rnorm)) {
+        st = set_error(h, HF_ERR_NONFINITE, "GMRES residual is not finite");
+        break;
+      }
+      if (rnorm <= tol || total >= o.max_iters) break;
+      if ((st = run_cycle<double, DIM>(h, K, h->J64.dg, h->J64.off, mrest, &h->graph64, &h->gev64))) break;
+      if ((st = read_gs(h, &ci))) break;
+      if (o.use_graphs) prof_flush_graph(h, h->gev64, ci.iters);
+      total += ci.iters;
+    }
+    cudaMemcpyAsync(x, K.x, N * sizeof(double), cudaMemcpyDeviceToDevice, h->stream);
+  }
   if (rep) {
     rep->gmres_iters = total;
     rep->refinements = refinements;
+    rep->fp64_fallback = fell_back ? 1 : 0;
     rep->lin_res = rnorm / bnorm;
     rep->lin_converged = rnorm <= tol;
   }

@@ -58,7 +58,9 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
     does not converge within newton_max iterations (or turns non-finite) is
     undone and retried with half the sub-step, which grows back by 1.5 after
     each accepted sub-step until t + dt is reached; at most max_cutbacks
-    failures in a row, 256 attempts in all."""
+    failures in a row, 256 attempts in all.  Past newton_max an attempt goes
+    on while the increments at least halve every iteration (at most
+    4 newton_max iterations)."""
     dt0 = o.prm.dt
     target = o.t + dt0
     sub = dt0
@@ -72,7 +74,7 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
     while target - o.t > 1e-12 * dt0:
         sub = min(sub, target - o.t)
         o.prm.dt = sub
-        ok, rounds, it = False, 0, 0
+        ok, rounds, it, prev = False, 0, 0, np.inf
         while True:
             r = o.newton_step()
             rep["newton_iters"] += 1
@@ -85,10 +87,12 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
                 if n_new == 0 or rounds >= rounds_max:
                     ok = True
                     break
-                it = 0
+                it, prev = 0, np.inf
                 continue
-            if it >= newton_max:
+            inc = max(r["du_rel"], r["dp_rel"])
+            if it >= newton_max and (it >= 4 * newton_max or not inc <= 0.5 * prev):
                 break
+            prev = inc
         attempts += 1
         if ok:
             o.accept_step()
