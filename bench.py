@@ -118,7 +118,7 @@ def make_problem(wl, precision, stream_ptr, G, restart):
     g = HFMesh.from_mesh(wl.mesh, stream=stream_ptr)
     inj, wts = wl.injection()
     g.hf_set_material(wl.E, wl.nu, wl.sigma_c, wl.delta_c, wl.b_stab)
-    g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.mesh.length)
+    g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.fluid_length)
     g.hf_set_solver(precision=precision, restart=restart, rtol=1e-8, inner_rtol=1e-3, max_iters=3000,
                     jacobi_block=G, newton_tol=1e-8)
     return g
@@ -152,7 +152,7 @@ class NewtonLoop:
         wl = self.wl
         inj, wts = wl.injection()
         self.dt = dt
-        self.g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, dt, 0.0, True, wl.mesh.length)
+        self.g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, dt, 0.0, True, wl.fluid_length)
 
     def _restart_step(self):
         U, P, a, b, w, t = self.saved
@@ -394,7 +394,7 @@ def oracle_baseline(wl, budget_s):
     inj, wts = wl.injection()
     t0 = time.perf_counter()
     prm = Params(E=wl.E, nu=wl.nu, sigma_c=wl.sigma_c, delta_c=wl.delta_c, b_stab=wl.b_stab, mu=wl.mu, Q0=wl.Q0,
-                 inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=wl.delta_f, dt=wl.dt, L_ref=wl.mesh.length)
+                 inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=wl.delta_f, dt=wl.dt, L_ref=wl.fluid_length)
     o = Oracle(wl.mesh, prm)
     U, P, al, be = wl.seed()
     o.set_state(U, P, al, be)

@@ -29,6 +29,11 @@ class Workload:
     seed_radius: float = 0.0
     w0: float = 1e-3
     p0: float = 1e6
+    L_ref: float = 0.0      # length L of the fluid-row scaling c = 12 mu (L / max w)^3; 0: the domain side
+
+    @property
+    def fluid_length(self):
+        return self.L_ref if self.L_ref > 0 else self.mesh.length
 
     @property
     def G_c(self):
@@ -109,6 +114,16 @@ def sample_parameters(rng):
             "mu": _log_uniform(rng, 1e-3, 1.0), "Q0": _log_uniform(rng, 1e-4, 1e-2)}
 
 
+def balanced_fluid_length(wl: Workload, w=None) -> float:
+    """Length L for which the fluid-row scaling c = 12 mu (L / w)^3 equals
+    E dt / h at opening w (the seed opening by default): the factor that
+    brings the pressure rows of the Newton system to the size of the
+    displacement rows (force ~ E h^(d-2) w against flux ~ c w h^(d-1) / dt)."""
+    h = wl.mesh.length / wl.mesh.n
+    w = wl.w0 if w is None else w
+    return w * (wl.E * wl.dt / (12.0 * wl.mu * h)) ** (1.0 / 3.0)
+
+
 def toughness_consistent(wl: Workload, sigma_c_max=1e6, zone_elems=4.0) -> Workload:
     """The same instance with a seed and a cohesive strength that its
     parameters can support, for draws over wide parameter ranges:
@@ -120,7 +135,8 @@ def toughness_consistent(wl: Workload, sigma_c_max=1e6, zone_elems=4.0) -> Workl
       centre: 4 p0 a / E' in plane strain, 8 p0 a / (pi E') for the penny
       (E' = E / (1 - nu^2));
     * sigma_c is lowered below sigma_c_max where needed so that the cohesive
-      length E' G_c / sigma_c^2 = K_Ic^2 / sigma_c^2 spans zone_elems elements.
+      length E' G_c / sigma_c^2 = K_Ic^2 / sigma_c^2 spans zone_elems elements;
+    * the length L of the fluid-row scaling from balanced_fluid_length.
     """
     m = wl.mesh
     h = m.length / m.n
@@ -133,7 +149,8 @@ def toughness_consistent(wl: Workload, sigma_c_max=1e6, zone_elems=4.0) -> Workl
         p0 = wl.K_Ic * math.sqrt(math.pi) / (2.0 * math.sqrt(a))
         w0 = 8.0 * p0 * a / (math.pi * Ep)
     sigma_c = min(sigma_c_max, wl.K_Ic / math.sqrt(zone_elems * h))
-    return dataclasses.replace(wl, p0=p0, w0=w0, sigma_c=sigma_c)
+    out = dataclasses.replace(wl, p0=p0, w0=w0, sigma_c=sigma_c)
+    return dataclasses.replace(out, L_ref=balanced_fluid_length(out))
 
 
 def sweep_instances(count=256, seed=191110275, ne_range=(1000, 50000), steps=10, mesh_cache=None):

@@ -28,7 +28,7 @@ def measure(wl, precision, G, m, base, newton_iters=2, stream=None):
     try:
         inj, wts = wl.injection()
         g.hf_set_material(wl.E, wl.nu, wl.sigma_c, wl.delta_c, wl.b_stab)
-        g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.mesh.length)
+        g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.fluid_length)
         g.hf_set_solver(**{**base, "precision": precision, "jacobi_block": G, "restart": m})
         g.hf_set_state(*wl.seed())
         g.hf_newton_step()

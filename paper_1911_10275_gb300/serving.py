@@ -16,7 +16,7 @@ def request_args(wl, state=None, t0=0.0):
     U, P, al, be = state if state is not None else wl.seed()
     return dict(E=wl.E, nu=wl.nu, sigma_c=wl.sigma_c, delta_c=wl.delta_c, b_stab=wl.b_stab, mu=wl.mu, Q0=wl.Q0,
                 inj_dofs=inj, inj_weights=wts, delta_f=wl.delta_f, dt=wl.dt, p_vapor=0.0, cutoff_on=True,
-                L_ref=wl.mesh.length, U0=U, P0=P, alpha0=al, beta0=be, t0=t0)
+                L_ref=getattr(wl, "fluid_length", wl.mesh.length), U0=U, P0=P, alpha0=al, beta0=be, t0=t0)
 
 
 def submit_workload(rt, wl, n_steps, solver=None, step=None, state=None):

@@ -9,7 +9,7 @@ def oracle_for(wl, fluid_scaling=True, cutoff=False):
     inj, wts = wl.injection()
     prm = Params(E=wl.E, nu=wl.nu, sigma_c=wl.sigma_c, delta_c=wl.delta_c, b_stab=wl.b_stab, mu=wl.mu,
                  Q0=wl.Q0, inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=wl.delta_f, dt=wl.dt,
-                 L_ref=wl.mesh.length, fluid_scaling=fluid_scaling, cutoff_on=cutoff)
+                 L_ref=wl.fluid_length, fluid_scaling=fluid_scaling, cutoff_on=cutoff)
     return Oracle(wl.mesh, prm)
 
 
@@ -18,7 +18,7 @@ def gpu_for(wl, fluid_scaling=True, cutoff=False, **solver):
     inj, wts = wl.injection()
     g = HFMesh.from_mesh(wl.mesh)
     g.hf_set_material(wl.E, wl.nu, wl.sigma_c, wl.delta_c, wl.b_stab)
-    g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, cutoff, wl.mesh.length)
+    g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, cutoff, wl.fluid_length)
     opts = dict(rtol=1e-13, max_iters=20000, jacobi_block=16, fluid_scaling=int(fluid_scaling))
     opts.update(solver)
     g.hf_set_solver(**opts)

@@ -2,10 +2,12 @@
 loop, its cutback path, the device-memory bound, and the request loop
 (hf_runtime_*): admission by budget, and every result the same alone and in
 a mix of concurrent requests."""
+import dataclasses
+
 import numpy as np
 import pytest
 
-from hf_inputs import kgd_2d, penny_3d
+from hf_inputs import kgd_2d, penny_3d, balanced_fluid_length
 from _setup import oracle_for, gpu_for, rel_err, oracle_advance_step
 
 pytestmark = pytest.mark.gpu
@@ -94,7 +96,8 @@ def _mix():
         (kgd_2d(n=10, length=20.0, E=15e9, K_Ic=1.5e6), {"precision": "mixed", "jacobi_block": 8}),
     ]
     base = {"rtol": 1e-10, "inner_rtol": 1e-3, "max_iters": 5000, "jacobi_block": 16, "newton_tol": 1e-9}
-    return [(wl, {**base, **s}) for wl, s in reqs]
+    # fluid rows at the scale of the displacement rows (see balanced_fluid_length)
+    return [(dataclasses.replace(wl, L_ref=balanced_fluid_length(wl)), {**base, **s}) for wl, s in reqs]
 
 
 def _run(rt, reqs, steps=2):
@@ -154,13 +157,14 @@ def test_admission_keeps_device_memory_within_budget():
 
 
 def test_mixed_solve_falls_back_to_fp64_when_fp32_stalls():
-    """A KGD instance of the sweep whose FP32 sweeps stall (a soft cohesive
-    law on a 36 x 36 mesh): the mixed solve hands over to FP64 and reaches the
-    tolerance, as the FP64 solve does.  (The two updates differ by a few per
-    cent: on this system a relative residual of 1e-8 bounds the error only
-    through a condition number above 1e6.)"""
+    """A KGD instance of the sweep with its fluid rows scaled by the domain
+    side instead of the balanced length (pressure rows ~1e7 times the force
+    rows): its FP32 sweeps stall, the mixed solve hands over to FP64 and
+    reaches the tolerance, as the FP64 solve does.  (The two updates differ by
+    a few per cent: on this system a relative residual of 1e-8 bounds the
+    error only through a condition number above 1e6.)"""
     from hf_inputs import sweep_instances
-    wl = sweep_instances(2)[1]
+    wl = dataclasses.replace(sweep_instances(2)[1], L_ref=0.0)
     states = []
     reps = []
     for prec in ("mixed", "fp64"):
