@@ -102,8 +102,9 @@ typedef struct {
   int use_graphs;       /* 1: capture each GMRES cycle in a CUDA graph */
   int coarse;           /* 1: add the rigid-body coarse correction to the preconditioner */
   int coarse_max;       /* bound on the coarse unknowns (16..4096): sets the aggregate size */
-  int reorth;           /* 1 (default): classical Gram-Schmidt with a second, re-orthogonalising
-                           pass; FP32 cycles lose orthogonality without it */
+  int reorth;           /* classical Gram-Schmidt passes: 0 one; 1 (default) a second,
+                           re-orthogonalising pass when the first removed more than 30% of the
+                           vector; 2 always two.  FP32 cycles lose orthogonality with one */
 } hf_solver_opts;
 
 /* Report of one Newton iteration (Sec. 3: convergence on the Euclidean norms

@@ -825,7 +825,7 @@ hf_status hf_set_solver(hf_mesh* h, const hf_solver_opts* o) {
   HF_GUARD(h);
   if (!o || (o->precision != HF_PREC_FP64 && o->precision != HF_PREC_MIXED) || o->restart < 1 || o->restart > GM_MAX ||
       o->max_iters < 0 || !(o->rtol > 0) || !(o->inner_rtol > 0) || o->jacobi_block < 1 || o->coarse < 0 ||
-      o->coarse > 1 || o->coarse_max < 16 || o->coarse_max > 4096 || o->reorth < 0 || o->reorth > 1)
+      o->coarse > 1 || o->coarse_max < 16 || o->coarse_max > 4096 || o->reorth < 0 || o->reorth > 2)
     return set_error(h, HF_ERR_INVALID_ARG, "solver options out of range");
   bool regroup = std::min(256, o->jacobi_block) != h->G;
   bool rescale = o->fluid_scaling != h->opts.fluid_scaling;

@@ -62,7 +62,7 @@ struct GmresState {
   int done;
   int jlast;
   int iters;
-  int pad;
+  int skip2;             // 1: the second Gram-Schmidt pass of this step is not needed
   double g[GM_LD];
   double h2[GM_LD];      // second Gram-Schmidt pass coefficients
   double cs[GM_MAX], sn[GM_MAX];

@@ -812,8 +812,11 @@ __device__ double block_sum_partials(const double* partial, int n, int stride, i
 // re-read per chunk, from L2)
 template <typename T>
 __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long ldv, int j, const T* __restrict__ w,
-                                             long long n, double* partial, int* counter, GmresState* gs, double* hout) {
-  if (gs->done) return;
+                                             long long n, double* partial, int* counter, GmresState* gs, double* hout,
+                                             int with_wnorm, const int* skipflag) {
+  // with_wnorm: also ||w||^2 into gs->nrm2 (partial column GM_MAX is free:
+  // at most GM_MAX coefficient columns); skipflag: leave at once if set
+  if (gs->done || (skipflag && *skipflag)) return;
   __shared__ double sm[RB / 32][32];
   __shared__ bool last;
   const int ncols = j + 1;
@@ -824,24 +827,30 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
   constexpr int CH = sizeof(T) == 4 ? 32 : 16;   // columns per transpose pass (static smem < 48 KB)
   __shared__ T tile[RB / 32][32][CH + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  double accw = 0.0;
   for (int q0 = 0; q0 < ncols; q0 += 32) {
     const int nq = min(32, ncols - q0);
     const T* Vq = V + (long long)q0 * ldv;
+    const bool wn = with_wnorm && q0 == 0;
     T acc[32];
+    T aw = (T)0;
 #pragma unroll
     for (int c = 0; c < 32; ++c) acc[c] = (T)0;
     for (long long iv = tid; iv < nv; iv += stride) {
       VT wv = reinterpret_cast<const VT*>(w)[iv];
+      if (wn) aw += Vec<T>::dot(wv, wv);
 #pragma unroll
       for (int c = 0; c < 32; ++c)
         if (c < nq) acc[c] += Vec<T>::dot(reinterpret_cast<const VT*>(Vq + c * ldv)[iv], wv);
     }
     for (long long i = nv * VN + tid; i < n; i += stride) {
       T wv = w[i];
+      if (wn) aw += wv * wv;
 #pragma unroll
       for (int c = 0; c < 32; ++c)
         if (c < nq) acc[c] += Vq[c * ldv + i] * wv;
     }
+    accw += (double)aw;
     // block reduction by transposition: warp w writes its 32 accumulators as
     // row lane of a 32x32 tile; lane c then adds column c (working precision,
     // 32 adds) and the warp results meet in double
@@ -866,6 +875,17 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
     }
     __syncthreads();
   }
+  if (with_wnorm) {
+    __shared__ double smw[RB / 32];
+    const double v = warp_sum(accw);
+    if (lane == 0) smw[warp] = v;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int wq = 0; wq < RB / 32; ++wq) s += smw[wq];
+      partial[(long long)blockIdx.x * GM_LD + GM_MAX] = s;
+    }
+  }
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
@@ -888,6 +908,11 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
       }
       __syncthreads();
     }
+    if (with_wnorm && threadIdx.x == 0) {
+      double s = 0.0;
+      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (long long)b * GM_LD + GM_MAX);
+      gs->nrm2 = s;
+    }
     if (threadIdx.x == 0) *counter = 0;
   }
 }
@@ -896,10 +921,14 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
 template <typename T>
 __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
                                              double* partial, int* counter, GmresState* gs, int mrest,
-                                             const double* hsrc, int accumulate) {
-  // w -= V hsrc; with accumulate (second Gram-Schmidt pass, hsrc = gs->h2)
-  // the coefficients are added to column j of H before the Givens update
-  if (gs->done) return;
+                                             const double* hsrc, int mode, double eta, const int* skipflag) {
+  // w -= V hsrc, ||w||, then the Givens update of column j, by mode:
+  //   0: single pass;
+  //   1: second pass (hsrc = gs->h2, added to column j of H first);
+  //   2: first of two passes: if ||w|| kept at least eta of its length before
+  //      the pass (gs->nrm2), no second pass is needed: finish here and set
+  //      gs->skip2; otherwise leave column j to the second pass
+  if (gs->done || (skipflag && *skipflag)) return;
   __shared__ T h[GM_MAX];
   const int ncols = j + 1;
   for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) h[c] = c < ncols ? (T)hsrc[c] : (T)0;
@@ -927,7 +956,16 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
   if (threadIdx.x == 0) {
     double nrm = sqrt(nrm2);
     double* hc = gs->H + j * GM_LD;
-    if (accumulate)
+    if (mode == 2) {
+      const double before = sqrt(gs->nrm2);
+      const bool enough = nrm >= eta * before || !(before > 0.0);
+      gs->skip2 = enough ? 1 : 0;
+      if (!enough) {
+        *counter = 0;
+        return;
+      }
+    }
+    if (mode == 1)
       for (int i = 0; i <= j; ++i) hc[i] += hsrc[i];
     for (int i = 0; i < j; ++i) {
       double a = hc[i], b = hc[i + 1];
@@ -948,32 +986,6 @@ __global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long 
     gs->jlast = j + 1;
     if (fabs(gs->g[j + 1]) <= gs->tol_abs || j + 1 >= mrest || !(nrm > 0.0) || !isfinite(nrm)) gs->done = 1;
     *counter = 0;
-  }
-}
-
-// first pass of classical Gram-Schmidt with reorthogonalisation: w -= V H[:, j]
-template <typename T>
-__global__ void __launch_bounds__(RB) k_orth_sub(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
-                                                 const GmresState* gs) {
-  if (gs->done) return;
-  __shared__ T h[GM_MAX];
-  const int ncols = j + 1;
-  for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) h[c] = c < ncols ? (T)gs->H[j * GM_LD + c] : (T)0;
-  __syncthreads();
-  using VT = typename Vec<T>::type;
-  constexpr int VN = Vec<T>::n;
-  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const long long nv = n / VN;
-  for (long long iv = tid; iv < nv; iv += stride) {
-    VT ww = reinterpret_cast<const VT*>(w)[iv];
-#pragma unroll 8
-    for (int c = 0; c < ncols; ++c) Vec<T>::axpy(ww, h[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
-    reinterpret_cast<VT*>(w)[iv] = ww;
-  }
-  for (long long i = nv * VN + tid; i < n; i += stride) {
-    T ww = w[i];
-    for (int c = 0; c < ncols; ++c) ww -= h[c] * V[c * ldv + i];
-    w[i] = ww;
   }
 }
 
@@ -1405,13 +1417,15 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
     spmv<T, DIM, 0>(h, dg, off, K.z, K.w, done);
     prof_end(h);
     prof_begin(h, PK_ORTH);
-    { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->H + j * GM_LD); }
-    if (h->opts.reorth) {
-      { note_launch(); k_orth_sub<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, gs); }
-      { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->h2); }
-      { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->h2, 1); }
-    } else {
-      { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->H + j * GM_LD, 0); }
+    const bool two = h->opts.reorth > 0;
+    // reorth 1: a second pass only when the first removed more than 30% of
+    // ||w|| (the Daniel-Gragg-Kaufman-Stewart test); reorth 2: always
+    const double eta = h->opts.reorth == 2 ? HUGE_VAL : 0.7;
+    { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->H + j * GM_LD, two ? 1 : 0, nullptr); }
+    { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->H + j * GM_LD, two ? 2 : 0, eta, nullptr); }
+    if (two) {
+      { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->h2, 0, &gs->skip2); }
+      { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->h2, 1, eta, &gs->skip2); }
     }
     { note_launch(); k_scale_into<T><<<rb, RB, 0, h->stream>>>(K.w, K.V + (long long)(j + 1) * K.ldv, N, &gs->inv_h, done); }
     prof_end(h);

@@ -121,3 +121,27 @@ def test_generators_are_seeded_and_in_range():
     assert np.all(np.diff(t) > 0) and abs(np.mean(np.diff(t)) - 1 / 200.0) < 2.5e-3
     dims = {w.mesh.dim for w in r}
     assert dims == {2, 3}
+
+
+def test_drawn_instances_are_toughness_consistent_and_balanced():
+    """The seed of a drawn instance sits at its toughness (K_I = K_Ic from the
+    plane-strain or penny formula), its opening is the elastic one of that
+    pressure, the cohesive length spans four elements, and the fluid rows
+    are scaled to c = E dt / h at the seed opening."""
+    import math
+    from hf_inputs import toughness_consistent, balanced_fluid_length
+    for wl in (kgd_2d(n=20, K_Ic=0.3e6, E=9e9, mu=0.2), penny_3d(n=6, K_Ic=2e6, E=30e9, mu=1e-3)):
+        t = toughness_consistent(wl, sigma_c_max=1e6)
+        a, h = t.seed_radius, t.mesh.length / t.mesh.n
+        Ep = t.E / (1 - t.nu ** 2)
+        if t.mesh.dim == 2:
+            assert abs(t.p0 * math.sqrt(math.pi * a) - t.K_Ic) < 1e-9 * t.K_Ic
+            assert abs(t.w0 - 4 * t.p0 * a / Ep) < 1e-12 * t.w0
+        else:
+            assert abs(2 * t.p0 * math.sqrt(a / math.pi) - t.K_Ic) < 1e-9 * t.K_Ic
+            assert abs(t.w0 - 8 * t.p0 * a / (math.pi * Ep)) < 1e-12 * t.w0
+        assert t.sigma_c <= 1e6 and t.K_Ic ** 2 / t.sigma_c ** 2 >= 4 * h * (1 - 1e-12)
+        c = 12 * t.mu * (t.fluid_length / t.w0) ** 3
+        assert abs(c - t.E * t.dt / h) < 1e-9 * c
+        assert t.fluid_length == balanced_fluid_length(t)
+    assert kgd_2d(n=8).fluid_length == kgd_2d(n=8).mesh.length
