@@ -3,8 +3,8 @@
 on one GB300 (assembly + ILU(0) block-Jacobi GMRES), through the C ABI.
 
 Workload: 3D penny-shaped fracture, cube of 50 m side split into 18^3 cubes of
-six P2 tetrahedra (34,992 elements, 1,100,305 unknowns), point injection at
-the centre of z = 0, every interior facet crackable.  A step is one Newton
+six P2 tetrahedra (34,992 elements, 1,051,129 unknowns), point injection at
+the centre of z = 0, the facets of that plane crackable.  A step is one Newton
 iteration of the time-stepping loop (Newton until converged, fracture
 criterion, end of step); each linear solve is driven to a relative residual of
 1e-8.  The headline runs the FP32-inner / FP64-refinement path; the FP64 path
@@ -490,7 +490,8 @@ def run_serve(args):
     out = {"metric": "serving latency p99 (ms) under a Poisson request stream", "value": summ.get("p99_ms"),
            "unit": "ms", "n_gpus": 1, "higher_is_better": False, "mode": "serve", "data": "synthetic",
            "dtype": "f32-inner/f64-refinement" if args.precision == "mixed" else "f64",
-           "config": {"workload": "serving stream: KGD n in [50, 316] and penny n in [8, 22], 5 steps each"},
+           "config": {"workload": f"serving stream: KGD n in [50, 316] and penny n in [8, 22], "
+                                  f"{args.serve_requests} requests of {args.serve_steps} steps"},
            "serving": summ, "clocks": clocks}
     print(json.dumps(out))
 
