@@ -908,10 +908,11 @@ __global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long 
       }
       __syncthreads();
     }
-    if (with_wnorm && threadIdx.x == 0) {
-      double s = 0.0;
-      for (int b = 0; b < (int)gridDim.x; ++b) s += __ldcg(partial + (long long)b * GM_LD + GM_MAX);
-      gs->nrm2 = s;
+    if (with_wnorm) {
+      // all threads of the last block share the sum (a serial loop over the
+      // blocks' partials would chain hundreds of L2 loads)
+      const double s = block_sum_partials(partial + GM_MAX, gridDim.x, GM_LD, 0);
+      if (threadIdx.x == 0) gs->nrm2 = s;
     }
     if (threadIdx.x == 0) *counter = 0;
   }
