@@ -195,7 +195,7 @@ class NewtonLoop:
 
 
 def algorithmic_bytes(stats, dim, elt):
-    """Bytes one launch must move at minimum (stated in the design doc):
+    """Bytes one launch must move at minimum:
     SpMV: every stored element-block value once, x and y once, neighbour ids;
     preconditioner: diagonal inverses plus in-subdomain L/U blocks once, its
     input and output vector once."""

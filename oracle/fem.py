@@ -23,8 +23,7 @@ Serebrinsky, Radovitzky, arXiv 1911.10275), written as directly as possible:
   quadrature point (Sec. 3, activation of the TSL); beta at the end of the
   step from the opening exceeding delta_f (Remark in Sec. 3).
 
-Readings where the paper is silent are listed in the design doc and named in the
-docstrings below.  Quadrature rules come from library routines (numpy
+Readings where the paper is silent are named in the docstrings below.  Quadrature rules come from library routines (numpy
 Gauss-Legendre, scipy Gauss-Jacobi) combined as conical products; the sparse
 linear solve is scipy's direct LU.  There is no blocking, fusion or
 reordering beyond what the definitions state.
