@@ -145,3 +145,30 @@ def test_drawn_instances_are_toughness_consistent_and_balanced():
         assert abs(c - t.E * t.dt / h) < 1e-9 * c
         assert t.fluid_length == balanced_fluid_length(t)
     assert kgd_2d(n=8).fluid_length == kgd_2d(n=8).mesh.length
+
+
+def test_autotuner_picks_the_fastest_candidate_once_per_size_class(monkeypatch):
+    """The tuner measures each candidate once per (dimension, precision,
+    log2 unknowns) class and hands every workload of the class the fastest;
+    a candidate whose solve did not converge (infinite time) never wins."""
+    import math
+    from paper_1911_10275_gb300 import autotune
+    calls = []
+
+    def fake_measure(wl, precision, G, m, base, newton_iters=2, stream=None):
+        calls.append((wl.mesh.n, G, m))
+        return math.inf if (G, m) == (8, 60) else 1.0 / G + m / 1000.0
+    monkeypatch.setattr(autotune, "measure", fake_measure)
+    t = autotune.Tuner()
+    a, b, c = kgd_2d(n=18), kgd_2d(n=20), kgd_2d(n=40)
+    assert autotune.size_class(a, "mixed") == autotune.size_class(b, "mixed") != autotune.size_class(c, "mixed")
+    best = t.tune(a, "mixed")
+    assert best == min((cand for cand in autotune.CANDIDATES if cand != (8, 60)), key=lambda q: 1.0 / q[0] + q[1] / 1000.0)
+    n_first = len(calls)
+    assert n_first == len(autotune.CANDIDATES)
+    assert t.tune(b, "mixed") == best and len(calls) == n_first        # same class: cached
+    t.tune(c, "mixed")
+    assert len(calls) == 2 * n_first                                    # new class: measured
+    opts = t.solver_for(a, "mixed")
+    assert opts["jacobi_block"] == best[0] and opts["restart"] == best[1] and opts["precision"] == "mixed"
+    assert set(t.report()) == {"2d/mixed/2^%d" % autotune.size_class(w, "mixed")[2] for w in (a, c)}
