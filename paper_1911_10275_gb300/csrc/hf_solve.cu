@@ -271,7 +271,7 @@ __device__ __forceinline__ void spmv_group(const DevMesh& m, const T* __restrict
 }
 
 template <typename T, int DIM, int MODE>
-__global__ void __launch_bounds__(32 * SpmvGroups<DIM>::P, 5) k_spmv(DevMesh m, const T* __restrict__ dg,
+__global__ void __launch_bounds__(32 * SpmvGroups<DIM>::P, 4) k_spmv(DevMesh m, const T* __restrict__ dg,
                                                                    const T* __restrict__ off, const T* __restrict__ x,
                                                                    T* __restrict__ y, int eblocks, const int* skip) {
   if (skip && *skip) return;
