@@ -23,10 +23,12 @@ Serebrinsky, Radovitzky, arXiv 1911.10275), written as directly as possible:
   quadrature point (Sec. 3, activation of the TSL); beta at the end of the
   step from the opening exceeding delta_f (Remark in Sec. 3).
 
-Readings where the paper is silent are named in the docstrings below.  Quadrature rules come from library routines (numpy
-Gauss-Legendre, scipy Gauss-Jacobi) combined as conical products; the sparse
-linear solve is scipy's direct LU.  There is no blocking, fusion or
-reordering beyond what the definitions state.
+Readings where the paper is silent are named in the docstrings below.
+Quadrature rules come from library routines (numpy Gauss-Legendre, scipy
+Gauss-Jacobi) combined as conical products; the sparse linear solve is
+scipy's direct LU, or, where its fill-in does not fit in memory, the plain
+ILU(0)-preconditioned GMRES of oracle/iterative.py.  There is no blocking,
+fusion or reordering beyond what the definitions state.
 """
 from __future__ import annotations
 
@@ -465,9 +467,26 @@ class Oracle:
                          if int(self.m.face_elems[f, 0]) in touch or int(self.m.face_elems[f, 1]) in touch
                          or (self.m.face_crackable[f] and
                              any(self.pindex[int(g)] in want_p for g in self.fnodes[f]))]
+            neu = [(f, tb) for f, tb in zip(self.neu_faces, self.neu_traction)
+                   if int(self.m.face_elems[f, 0]) in touch]
         else:
             elem_list = range(self.ne)
             face_list = range(self.nf)
+            neu = list(zip(self.neu_faces, self.neu_traction))
+        R, coo = self.assemble_terms(U, P, elem_list, face_list, neu, with_jacobian)
+        J = None
+        if with_jacobian:
+            J = sp.coo_matrix((coo[2], (coo[0], coo[1])), shape=(self.N, self.N)).tocsr()
+        return self.finish_assembly(R, J, U, P)
+
+    def assemble_terms(self, U, P, elem_list, face_list, neu, with_jacobian=True):
+        """The sums of Eq. discreteElastoStatics and Eq. discreteLubrication
+        over the listed elements (bulk term), interior facets (DG, cohesive
+        and fluid terms) and Neumann facets ``neu`` = [(facet, traction)]:
+        R and the Jacobian entries as COO arrays (rows, cols, vals), without
+        the injection and the identity rows (``finish_assembly``).  Assembly
+        is a sum over elements and facets, so partial sums over a partition of
+        them add up to the whole."""
         p = self.prm
         d, ned = self.dim, self.ned
         R = np.zeros(self.N)
@@ -539,32 +558,40 @@ class Oracle:
                                                  + np.einsum("q,qg,qb->gb", wq, eta, njump[s]) / p.dt))
                     add(pdofs, pdofs, c * np.einsum("q,q,qgi,qhi->gh", wq, k3, geta, geta))
         # Neumann traction on outer facets
-        for f, tb in zip(self.neu_faces, self.neu_traction):
-            if sample and int(self.m.face_elems[f, 0]) not in touch:
-                continue
+        for f, tb in neu:
             e = int(self.m.face_elems[f, 0])
             x, wq = self.face_points(f)
             N, _ = self.elem_basis_at(e, x)
             R[self.udofs(e)] -= np.einsum("q,qa,k->ak", wq, N, tb).ravel()
+        if with_jacobian and rows:
+            coo = (np.concatenate(rows), np.concatenate(cols), np.concatenate(vals))
+        else:
+            coo = (np.zeros(0, np.int64), np.zeros(0, np.int64), np.zeros(0))
+        return R, coo
+
+    def finish_assembly(self, R, J, U=None, P=None):
+        """Adds the point injection to the summed terms and imposes the
+        identity rows (inactive pressures p = p_v, Dirichlet displacements)."""
+        U = self.U if U is None else U
+        P = self.P if P is None else P
+        p = self.prm
+        act = self.active_pdofs()
+        c = self.c_scale
         # injection (point source Q0 split by weights)
         for g, wgt in zip(p.inj_pdofs, p.inj_weights):
             R[self.Nu + g] -= c * p.Q0 * wgt
-        J = None
-        if with_jacobian:
-            J = sp.coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                              shape=(self.N, self.N)).tocsr()
         # identity rows: inactive pressures (p = p_v) and Dirichlet displacements
         ident = list(self.Nu + np.nonzero(~act)[0]) + list(self.m.dir_dof)
         ident = np.asarray(ident, dtype=np.int64)
         target = np.concatenate([np.full(int((~act).sum()), p.p_vapor), self.m.dir_val])
         cur = np.concatenate([P[~act], U[self.m.dir_dof]])
         R[ident] = cur - target
-        if with_jacobian and ident.size:
-            J = J.tolil()
-            for r in ident:
-                J.rows[r] = [int(r)]
-                J.data[r] = [1.0]
-            J = J.tocsr()
+        if J is not None and ident.size:
+            # row r of J becomes e_r^T: keep the other rows, add the unit diagonal
+            is_id = np.zeros(self.N)
+            is_id[ident] = 1.0
+            J = (sp.diags(1.0 - is_id) @ J.tocsr() + sp.diags(is_id)).tocsr()
+            J.eliminate_zeros()
         return R, J
 
     # ---------------------------------------------------------------- steps
@@ -588,9 +615,11 @@ class Oracle:
             x = x + c * lu.solve(r * (b - J @ x))
         return x
 
-    def newton_step(self, solve=None):
-        """One Newton iteration: J d = -R, update, relative increments."""
-        R, J = self.assemble()
+    def newton_step(self, solve=None, assemble=None):
+        """One Newton iteration: J d = -R, update, relative increments.
+        ``solve(J, b)`` replaces the direct solve and ``assemble()`` the
+        serial assembly (same definitions, other routes to them)."""
+        R, J = self.assemble() if assemble is None else assemble()
         d = self.solve_linear(J, -R) if solve is None else solve(J, -R)
         dU, dP = d[: self.Nu], d[self.Nu:]
         P_old = self.P

@@ -4,7 +4,7 @@
   Sec. 4.1: K = (12 mu Q0 E'^3)^(-1/4) * 8/sqrt(2 pi) * K_Ic and
   M = 12 mu Q0 E'^3 (8/sqrt(2 pi) K_Ic)^(-4); K = M^(-1/4).
   Regimes: viscosity-dominated for K < 0.70, toughness-dominated for K > 4.13.
-* Same numbers for the radial (penny) fracture, Sec. 4.3, which depend on t:
+* Same numbers for the radial (penny) fracture, Sec. 4.4, which depend on t:
   K = (t^2 / ((12 mu)^5 Q0^3 E'^13))^(1/18) * 8/sqrt(2 pi) K_Ic,
   M = 12 mu (Q0^3 E'^13 / t^2)^(1/5) (8/sqrt(2 pi) K_Ic)^(-18/5); M = K^(-18/5).
   Regimes: K < 0.37 viscosity, K > 3.5 toughness.
@@ -16,6 +16,8 @@
   V = pi p l^2 / E' * 2 = Q0 t  ->  l(t) = (E' Q0 t / (2 sqrt(pi) K_Ic))^(2/3).
 * Sneddon: opening of a crack of half-length l under uniform net pressure p in
   an infinite plane-strain body, w(x) = (4 p / E') sqrt(l^2 - x^2).
+* Zero-toughness (M-vertex) radial fracture, Sec. 4.4 (analytic solution of
+  the viscosity regime): R(t) = gamma_m0 (Q0^3 E' t^4 / mu')^(1/9), mu' = 12 mu.
 """
 import math
 
@@ -74,3 +76,11 @@ def k_vertex_pressure(Kic, length):
 
 def sneddon_opening(E, nu, p, length, x):
     return 4.0 * p / e_prime(E, nu) * math.sqrt(max(length * length - x * x, 0.0))
+
+
+def penny_m_vertex_radius(E, nu, mu, Q0, t, gamma_m0):
+    return gamma_m0 * (Q0 ** 3 * e_prime(E, nu) * t ** 4 / (12.0 * mu)) ** (1.0 / 9.0)
+
+
+def penny_m_vertex_gamma(E, nu, mu, Q0, t, radius):
+    return radius / penny_m_vertex_radius(E, nu, mu, Q0, t, 1.0)

@@ -92,3 +92,18 @@ def test_config_regime_labels():
     K = kgd.kgd_K(20e9, 0.2, 1e-3, 1e-3, 1e6)
     assert 0.70 < K < 4.13
     assert K == pytest.approx(0.989, abs=0.002)
+
+
+def test_penny_initial_radius_consistent_with_m_vertex():
+    """Sec. 4.4 starts the penny crack from the viscosity-regime analytic
+    solution with radius 10 m at 17.6 s: R = gamma_m0 (Q0^3 E' t^4/mu')^(1/9)
+    then fixes gamma_m0 ~ 0.70, the constant of the zero-toughness radial
+    similarity solution (0.6955 in the literature the paper cites)."""
+    mu, Q0 = 0.15, 0.03
+    g = kgd.penny_m_vertex_gamma(E, NU, mu, Q0, G["penny_t0"], G["penny_R0"])
+    assert 0.69 < g < 0.705
+    assert g == pytest.approx(0.6955, rel=0.01)
+    # R grows as t^(4/9): doubling t multiplies R by 2^(4/9)
+    r1 = kgd.penny_m_vertex_radius(E, NU, mu, Q0, 10.0, g)
+    r2 = kgd.penny_m_vertex_radius(E, NU, mu, Q0, 20.0, g)
+    assert r2 / r1 == pytest.approx(2.0 ** (4.0 / 9.0), rel=1e-12)

@@ -281,6 +281,9 @@ def test_finite_difference_tangent_all_three_states(dim):
 
 
 def test_sparse_solve_equals_dense_brute_force():
+    """The library sparse LU and a dense LU of the same raw system agree (the
+    oracle's own equilibrated solve is pinned against a 40-digit solve in
+    test_oracle_iterative.py)."""
     m, o = _kgd_setup(n=2, L=4.0, radius=2.01)
     assert o.beta.sum() == 2
     R, J = o.assemble()
@@ -288,16 +291,6 @@ def test_sparse_solve_equals_dense_brute_force():
     xd = np.linalg.solve(J.toarray(), -R)
     for sl in (slice(0, o.Nu), slice(o.Nu, o.N)):
         assert np.abs(xs[sl] - xd[sl]).max() <= 1e-10 * np.abs(xd[sl]).max()
-    # the oracle's solve (equilibrated LU + refinement) against a dense solve of
-    # the equilibrated system in extended precision
-    Jd = J.toarray()
-    r = 1.0 / np.abs(Jd).max(axis=1)
-    c = 1.0 / np.abs(Jd * r[:, None]).max(axis=0)
-    A = np.asarray(Jd * r[:, None] * c[None, :], dtype=np.longdouble)
-    xe = c * np.asarray(np.linalg.solve(A.astype(np.float64), (-R * r)), dtype=np.float64)
-    xo = o.solve_linear(J, -R)
-    for sl in (slice(0, o.Nu), slice(o.Nu, o.N)):
-        assert np.abs(xo[sl] - xe[sl]).max() <= 1e-11 * np.abs(xe[sl]).max()
 
 
 # ------------------------------------------------------------------ invariants
@@ -438,3 +431,161 @@ def test_sampled_assembly_rows_equal_global_rows():
     assert np.array_equal(Rs[rows], R[rows])
     x = rng.standard_normal(o.N)
     assert np.allclose((Js @ x)[rows], (J @ x)[rows], rtol=1e-14, atol=0)
+
+
+# ------------------------------------------------------------------ 3D lubrication, TSL branches, cut-off
+def _penny_setup(dt=0.5, Q0=1e-2, **kw):
+    m = cube_p2(2, 8.0, crackable="plane")
+    U, P, al, be = seed_state(m, radius=4.1, w0=1e-3, p0=1e6)
+    pn = pressure_nodes(m)
+    inj = int(np.nonzero(pn == m.center_node)[0][0])
+    o = Oracle(m, _params(L_ref=8.0, inj_pdofs=(inj,), inj_weights=(1.0,), dt=dt, Q0=Q0, **kw))
+    o.set_state(U, P, al, be)
+    return m, o
+
+
+def test_discrete_volume_invariant_3d():
+    """3D counterpart of the volume pin: the P2 traces of a triangular facet
+    sum to one, so their surface gradients cancel the conduction term only if
+    the gradient is projected on the facet plane; at convergence the crack
+    volume then grows by exactly Q0 dt (no leak-off, Eq. lubrication)."""
+    m, o = _penny_setup()
+
+    def volume(w_of):
+        v = 0.0
+        for f in np.nonzero(o.beta)[0]:
+            x, wq = o.face_points(f)
+            v += np.sum(wq * w_of(f, x))
+        return v
+
+    v_old = volume(lambda f, x: o.pressure_trace(f, x)[0] @ o.w_old[f])
+    for _ in range(12):
+        rep = o.newton_step()
+        if rep["converged"]:
+            break
+    assert rep["converged"]
+    v_new = volume(lambda f, x: o.face_kinematics(f, o.U)[-1])
+    assert v_new - v_old == pytest.approx(o.prm.Q0 * o.prm.dt, rel=1e-10)
+
+
+# P2 matrices of the reference right triangle (legs 1), vertices (0,0),
+# (1,0), (0,1), mid-nodes (1/2,0), (1/2,1/2), (0,1/2): the Laplacian
+# stiffness (scale-invariant in 2D) and the mass matrix / area, the textbook
+# values (derived independently by exact symbolic integration of the
+# monomial-basis P2 functions).
+P2TRI_STIFF = np.array([[6, 1, 1, -4, 0, -4], [1, 3, 0, -4, 0, 0], [1, 0, 3, 0, 0, -4],
+                        [-4, -4, 0, 16, -8, 0], [0, 0, 0, -8, 16, -8], [-4, 0, -4, 0, -8, 16]]) / 6.0
+P2TRI_MASS_PER_AREA = np.array([[6, -1, -1, 0, -4, 0], [-1, 6, -1, 0, 0, -4], [-1, -1, 6, -4, 0, 0],
+                                [0, 0, -4, 32, 16, 16], [-4, 0, 0, 16, 32, 16], [0, -4, 0, 16, 16, 32]]) / 180.0
+
+
+def _right_triangle_roles(X):
+    """Order of the 6 face nodes (coordinates X, vertices first) that matches
+    the reference right triangle: right-angle vertex, the other two, then the
+    mid-nodes of (v0,v1), (v1,v2), (v2,v0)."""
+    for r in range(3):
+        a, b = [i for i in range(3) if i != r]
+        if abs(np.dot(X[a] - X[r], X[b] - X[r])) < 1e-9 * np.dot(X[a] - X[r], X[a] - X[r]):
+            break
+    v = [r, a, b]
+    def mid(i, j):
+        c = 0.5 * (X[i] + X[j])
+        return 3 + int(np.argmin(np.linalg.norm(X[3:] - c, axis=1)))
+    return v + [mid(v[0], v[1]), mid(v[1], v[2]), mid(v[2], v[0])]
+
+
+def test_textbook_p2_triangle_facet_matrices_3d():
+    """On a flat right-isosceles facet of a 3D mesh with uniform opening w and
+    P = 0: the pressure block is (w^3/12mu) times the P2 Laplacian stiffness
+    of the triangle, the storage part of C is (1/dt) n_k times the P2 mass
+    matrix, and B = -n_k times the mass matrix (Eq. discreteLubrication, Eq.
+    discreteElastoStatics)."""
+    m = cube_p2(2, 8.0, crackable="plane")
+    o = Oracle(m, _params(mu=1e-3, dt=0.5))
+    f = int(np.nonzero(m.face_crackable)[0][1])
+    em, ep = m.face_elems[f]
+    w0 = 3e-4
+    U = np.zeros(o.Nu)
+    n = o.normal[f]
+    for a in range(o.nn):
+        U[o.udofs(ep)[a * 3:(a + 1) * 3]] = w0 * n
+    al = np.zeros(o.nf, np.int8)
+    be = np.zeros(o.nf, np.int8)
+    al[f] = be[f] = 1
+    o.set_state(U, np.zeros(o.Np), al, be)
+    _, J = o.assemble()
+    J = J.toarray()
+    X = m.xyz[o.fnodes[f]]
+    perm = _right_triangle_roles(X)
+    pd = np.array([o.pindex[int(g)] for g in o.fnodes[f]])[perm]
+    area = o.area[f]
+    D = J[np.ix_(o.Nu + pd, o.Nu + pd)]
+    assert np.allclose(D, w0 ** 3 / 12e-3 * P2TRI_STIFF, rtol=1e-12, atol=1e-12 * w0 ** 3 / 12e-3)
+    mass = area * P2TRI_MASS_PER_AREA
+    order_p = [int(np.nonzero(m.elem_nodes[ep] == g)[0][0]) for g in o.fnodes[f][perm]]
+    for k in range(3):
+        cols = [o.udofs(ep)[a * 3 + k] for a in order_p]
+        C = J[np.ix_(o.Nu + pd, cols)]
+        assert np.allclose(C, mass * n[k] / 0.5, rtol=1e-12, atol=1e-12 * np.abs(mass).max() / 0.5)
+        B = J[np.ix_(cols, o.Nu + pd)]
+        assert np.allclose(B, -mass * n[k], rtol=1e-12, atol=1e-12 * np.abs(mass).max())
+
+
+def test_tsl_contact_branch_matches_intact_normal_stiffness():
+    """Reading of Eq. tsl for w < 0: the traction continues from sigma_c at
+    w = 0 with the slope of an intact facet's normal penalty (b/h) n.(C:(n x n)).n
+    = (b/h)(lambda + 2 mu), computed here from the elasticity tensor; the
+    derivative returned agrees with a finite difference on both sides of 0 and
+    of delta_c."""
+    for dim in (2, 3):
+        if dim == 2:
+            m, o = _kgd_setup()
+        else:
+            m, o = _penny_setup()
+        f = int(np.nonzero(m.face_crackable)[0][0])
+        n = o.normal[f]
+        C = fem.stiffness_tensor(o.prm.E, o.prm.nu, dim)
+        kn = o.prm.b_stab / o.hf[f] * np.einsum("i,ijkl,j,k,l->", n, C, n, n, n)
+        sc, dc = o.prm.sigma_c, o.prm.delta_c
+        eps = 1e-6 * dc
+        w = np.array([-3 * dc, -eps, 0.0, eps, 0.5 * dc, dc - eps, dc, dc + eps])
+        T, dT = o.tsl(w, f)
+        assert T[1] == pytest.approx(sc - kn * eps, rel=1e-12)
+        assert dT[0] == pytest.approx(kn, rel=1e-12) and dT[1] == pytest.approx(kn, rel=1e-12)
+        assert T[2] == pytest.approx(sc, rel=1e-15)
+        assert T[0] < 0.0 < T[2]                      # compression pushes the lips apart
+        assert T[5] == pytest.approx(sc * eps / dc, rel=1e-6) and T[6] == 0.0 and T[7] == 0.0
+        for wi in (-2 * dc, 0.5 * dc, 1.5 * dc):
+            h = 1e-4 * dc
+            Tp, _ = o.tsl(np.array([wi + h]), f)
+            Tm, _ = o.tsl(np.array([wi - h]), f)
+            _, d0 = o.tsl(np.array([wi]), f)
+            assert (Tp[0] - Tm[0]) / (2 * h) == pytest.approx(d0[0], rel=1e-8, abs=1e-12 * kn)
+
+
+def test_pressure_cutoff_converges_with_clipped_pressures():
+    """Reading of the vapour-pressure cut-off (Remark in Sec. 3): with fluid
+    withdrawn (Q0 < 0) the unclipped iteration drives the pressure far below
+    p_v = 0; with the cut-off every active pressure stays >= p_v, some sit
+    exactly at p_v, and Newton still converges because the increment measured
+    is the change applied to the nodal array (a pressure that stays clipped
+    stops changing)."""
+    m = square_p2(4, 8.0, crackable="midline")
+    U, P, al, be = seed_state(m, radius=8.0 / 4 * 1.01, w0=1e-3, p0=1e6)
+    pn = pressure_nodes(m)
+    inj = int(np.nonzero(pn == m.center_node)[0][0])
+    runs = {}
+    for cut in (True, False):
+        o = Oracle(m, _params(Q0=-1e-2, L_ref=8.0, fluid_scaling=True, inj_pdofs=(inj,), inj_weights=(1.0,),
+                              cutoff_on=cut, p_vapor=0.0, newton_tol=1e-10))
+        o.set_state(U, P, al, be)
+        for it in range(12):
+            rep = o.newton_step()
+            if rep["converged"]:
+                break
+        runs[cut] = (rep, o.P[o.active_pdofs()], it)
+    rep, Pa, it = runs[True]
+    assert rep["converged"] and it < 10
+    assert Pa.min() >= 0.0 and np.sum(Pa == 0.0) >= 1
+    rep_off, Pa_off, _ = runs[False]
+    assert not rep_off["converged"] and Pa_off.min() < -1e8
