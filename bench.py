@@ -103,12 +103,24 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
+# The timed solver settings.  GMRES tolerances are the loosest that keep every
+# Newton iterate within relative 1e-8 of the FP64 oracle's (openings,
+# pressures, displacements), as tests/test_gpu_accuracy.py checks along the
+# oracle's trajectory: FP32 inner sweeps reducing the residual 1e3-fold inside
+# FP64 refinement to 1e-11, and plain FP64 GMRES to 1e-11.
+HEADLINE = {"mixed": dict(precision="mixed", restart=60, reorth=3, rtol=1e-11, inner_rtol=1e-3),
+            "fp64": dict(precision="fp64", restart=60, reorth=3, rtol=1e-11, inner_rtol=1e-3)}
+COMMON = dict(jacobi_block=32, coarse=1, use_graphs=1, newton_tol=1e-8, max_iters=8000)
+
+
 def solver_kw(args, prec, graphs=None):
-    """Solver options of the timed path: GMRES to a relative residual of 1e-8,
-    each precision with its own cycle length and Gram-Schmidt passes."""
+    """Solver options of the timed path: GMRES to the relative residual of
+    each precision (--rtol, --fp64-rtol), each precision with its own cycle
+    length and Gram-Schmidt passes."""
     mixed = prec == "mixed"
     return dict(precision=prec, restart=args.restart if mixed else args.fp64_restart,
-                reorth=args.reorth if mixed else args.fp64_reorth, rtol=1e-8, inner_rtol=1e-3,
+                reorth=args.reorth if mixed else args.fp64_reorth, rtol=args.rtol if mixed else args.fp64_rtol,
+                inner_rtol=1e-3,
                 max_iters=args.max_iters, jacobi_block=args.jacobi_block, newton_tol=1e-8,
                 use_graphs=args.graphs if graphs is None else graphs, coarse=args.coarse)
 
@@ -194,19 +206,37 @@ class NewtonLoop:
         return rep
 
 
-def algorithmic_bytes(stats, dim, elt):
-    """Bytes one launch must move at minimum:
+def algorithmic_bytes(stats, dim, elt, nc=0):
+    """Bytes one launch must move at minimum, per kernel class:
     SpMV: every stored element-block value once, x and y once, neighbour ids;
-    preconditioner: diagonal inverses plus in-subdomain L/U blocks once, its
-    input and output vector once."""
+    preconditioner (ILU(0) apply): diagonal inverses plus in-subdomain L/U
+    blocks once, its input and output vector once, the 8-byte task records;
+    coarse level per apply: restriction (r and the nodal coordinates of the
+    modes), the dense inverse, prolongation (coordinates, z read and written)."""
     ned = 30 if dim == 3 else 12
     nfr = 18 if dim == 3 else 6
     ne = stats["elements"]
-    N = ne * ned + stats["n_p"]
+    nu = ne * ned
+    N = nu + stats["n_p"]
     spmv_vals = ne * ned * ned + stats["interior_slots"] * ned * nfr
     prec_vals = ne * ned * ned + stats["subdomain_slots"] * ned * nfr
     return {"spmv": spmv_vals * elt + 2 * N * elt + ne * (dim + 1) * 4,
-            "precond": prec_vals * elt + 2 * N * elt + ne * 8}
+            "precond": prec_vals * elt + 2 * N * elt + ne * 8,
+            "coarse": (nu * elt + nu * elt) + nc * nc * elt + (nu * elt + 2 * nu * elt) if nc else 0,
+            "N": N}
+
+
+def gs_bytes(N, elt, steps, cols, reorths, reorth_cols, reorth_mode):
+    """Algorithmic bytes of the Gram-Schmidt kernels over `steps` Arnoldi
+    steps (cols = the sum of j + 1 over them).  Delayed CGS2 (mode 3) streams
+    the j final basis vectors twice per step (the fused dot products, then
+    the fused update) and the lagged vector and w twice each, and writes v_j
+    and the next lagged vector: 2 j + 6 vectors.  Classical Gram-Schmidt
+    streams the j + 1 vectors twice per pass and w five times; a second pass
+    adds two basis sweeps and three of w."""
+    if reorth_mode == 3:
+        return N * elt * (2 * (cols - steps) + 6 * steps)
+    return N * elt * (2 * cols + 5 * steps + 2 * reorth_cols + 3 * reorths)
 
 
 def traffic_from_profiles(kernel):
@@ -218,6 +248,39 @@ def traffic_from_profiles(kernel):
         return d.get(kernel)
     except Exception:
         return None
+
+
+GOLDEN = {"c3_penny3d_n18_mixed": os.path.join(ROOT, "tests", "golden", "c3_newton_oracle.json")}
+
+
+def load_golden(wl):
+    """The oracle's trajectory of this workload, written by
+    tests/golden/make_c3_newton.py (oracle only), or None."""
+    p = GOLDEN.get(wl.name)
+    if not p or not os.path.exists(p):
+        return None
+    with open(p) as f:
+        return json.load(f)
+
+
+def errors_vs_golden(rec, u_idx, U, P, W):
+    """Relative errors of one Newton iterate against the oracle's: U on the
+    stored sample of unknowns, every non-zero oracle pressure, the openings at
+    the face nodes of every cohesive or fluid facet, each over the infinity
+    norm of the oracle's full field."""
+    eu = float(np.abs(U[u_idx] - np.asarray(rec["U"])).max() / rec["U_inf"])
+    pi = np.asarray(rec["P_index"], dtype=np.int64)
+    ep = float(np.abs(P[pi] - np.asarray(rec["P"])).max() / rec["P_inf"]) if pi.size else 0.0
+    wf = np.asarray(rec["w_faces"], dtype=np.int64)
+    ew = float(np.abs(W[wf] - np.asarray(rec["w"])).max() / rec["w_inf"]) if wf.size else 0.0
+    return {"U": eu, "P": ep, "w": ew}
+
+
+def _reset(g, wl, seed):
+    """Back to the seed state at t = 0 with the full time step."""
+    inj, wts = wl.injection()
+    g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.fluid_length)
+    g.hf_set_state(*seed)
 
 
 def run_ours(args):
@@ -234,16 +297,20 @@ def run_ours(args):
     prec = "mixed" if args.precision == "mixed" else "fp64"
     g = make_problem(wl, prec, stream.cuda_stream, args.jacobi_block, args.restart)
     g.hf_set_solver(**solver_kw(args, prec))
-    U, P, al, be = wl.seed()
-    g.hf_set_state(U, P, al, be)
+    seed = wl.seed()
+    golden = load_golden(wl)
+
+    # warm-up: the first W Newton iterations of the time loop (graphs captured)
+    _reset(g, wl, seed)
     loop = NewtonLoop(g, wl)
     for _ in range(args.warmup):
         loop.step()
-    stats = g.hf_get_stats()
-    launches0 = stats["kernel_launches"]
-    g.hf_set_profiling(True)
-    loop.reports.clear()
-    loop.latencies.clear()
+
+    # timed region: the first K Newton iterations of the time loop again, from
+    # the same seed state, state resident on the device
+    _reset(g, wl, seed)
+    loop = NewtonLoop(g, wl)
+    st0 = g.hf_get_stats()
     sampler = ClockSampler(local)
     sampler.start()
     if world > 1:
@@ -259,24 +326,8 @@ def run_ours(args):
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = ev0.elapsed_time(ev1)
-    ktimes = g.hf_get_kernel_times()
-    g.hf_set_profiling(False)
-    timing_source = "CUDA events on the library stream inside the timed region"
-    if args.graphs and ktimes["spmv"][1] == 0:
-        # this driver/toolkit gave no timing for events recorded inside graphs:
-        # time the kernels with events on the same state, graphs off, right after
-        code = g.hf_get_stats()["graph_timing_error"]
-        g.hf_set_solver(**solver_kw(args, prec, graphs=0))
-        g.hf_set_profiling(True)
-        for _ in range(2):
-            loop.step()
-        ktimes = g.hf_get_kernel_times()
-        g.hf_set_profiling(False)
-        g.hf_set_solver(**solver_kw(args, prec))
-        timing_source = ("CUDA events over 2 Newton iterations right after the timed region, same state, "
-                         f"graphs off (graph-node event timing unavailable: CUDA error {code})")
-    stats = g.hf_get_stats()
-    launches = stats["kernel_launches"] - launches0
+    st1 = g.hf_get_stats()
+    launches = st1["kernel_launches"] - st0["kernel_launches"]
     reports = list(loop.reports)
     lat = sorted(loop.latencies)
     if world > 1:
@@ -285,38 +336,108 @@ def run_ours(args):
         ms = float(t.item())
     value = args.steps * world / (ms / 1000.0)
 
-    # end to end through the public API with host buffers: the same time
-    # loop, but every step uploads the state from pinned host memory and reads
-    # the updated state back
+    # kernel classes: the same trajectory once more with CUDA events around
+    # every kernel class on the library's stream (graphs off: events recorded
+    # inside captured graphs give no timings on this toolkit), at least 10
+    # iterations
+    n_prof = max(10, args.steps)
+    g.hf_set_solver(**solver_kw(args, prec, graphs=0))
+    _reset(g, wl, seed)
+    lp = NewtonLoop(g, wl)
+    sp0 = g.hf_get_stats()
+    g.hf_set_profiling(True)
+    for _ in range(n_prof):
+        lp.step()
+    ktimes = g.hf_get_kernel_times()
+    g.hf_set_profiling(False)
+    sp1 = g.hf_get_stats()
+    g.hf_set_solver(**solver_kw(args, prec))
+    arnoldi = sum(r["gmres_iters"] for r in lp.reports)
+    elt = 4 if prec == "mixed" else 8
+    algo = algorithmic_bytes(st1, wl.mesh.dim, elt, st1.get("coarse_unknowns", 0))
+    N = algo["N"]
+    orth_bytes = gs_bytes(N, elt, arnoldi, sp1["gs_cols"] - sp0["gs_cols"], sp1["gs_reorths"] - sp0["gs_reorths"],
+                          sp1["gs_reorth_cols"] - sp0["gs_reorth_cols"], args.reorth if prec == "mixed" else args.fp64_reorth)
+    peak, peak_src = peaks()
+    cls = {
+        "spmv": (algo["spmv"] * ktimes["spmv"][1], ktimes["spmv"][0], ktimes["spmv"][1],
+                 f"k_spmv<{'float' if elt == 4 else 'double'},3,0>"),
+        "precond": (algo["precond"] * ktimes["precond"][1], ktimes["precond"][0], ktimes["precond"][1],
+                    f"k_ilu_apply<{'float' if elt == 4 else 'double'},3>"),
+        "orth": (orth_bytes, ktimes["orth"][0], ktimes["orth"][1],
+                 (f"k_dc_dot/k_dc_upd<{'float' if elt == 4 else 'double'}> (delayed CGS2)" if
+                  (args.reorth if prec == "mixed" else args.fp64_reorth) == 3 else
+                  f"k_gs_dot/k_gs_sub/k_gs_fin<{'float' if elt == 4 else 'double'}> (Gram-Schmidt)")),
+        "precond_aux": (algo["coarse"] * ktimes["precond"][1], ktimes["precond_aux"][0], ktimes["precond_aux"][1],
+                        "coarse level + pressure rows"),
+    }
+    dom = max(cls, key=lambda k: cls[k][1])
+    b_dom, ms_dom, n_dom, kname = cls[dom]
+    achieved = b_dom / (ms_dom / 1000.0) / 1e9 if ms_dom > 0 else 0.0
+    roofline = {"bound": "hbm", "kernel": kname, "class": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "peak_source": peak_src, "algorithmic_bytes": int(b_dom),
+                "launches": n_dom, "ms": ms_dom, "traffic": traffic_from_profiles(kname.split(" ")[0])}
+    sol_bytes = sum(v[0] for v in cls.values())
+    sol_ms = sum(v[1] for v in cls.values())
+    solve_phase = {"classes": {k: {"GB": round(v[0] / 1e9, 3), "ms": round(v[1], 3), "launches": v[2],
+                                   "GB_s": round(v[0] / (v[1] / 1e3) / 1e9, 1) if v[1] else None}
+                               for k, v in cls.items()},
+                   "arnoldi_steps": arnoldi, "GB_per_arnoldi_step": round(sol_bytes / max(arnoldi, 1) / 1e9, 4),
+                   "us_per_arnoldi_step": round(1000.0 * sol_ms / max(arnoldi, 1), 2),
+                   "achieved": sol_bytes / (sol_ms / 1000.0) / 1e9 if sol_ms else 0.0, "peak": peak,
+                   "frac": (sol_bytes / (sol_ms / 1000.0) / 1e9) / peak if sol_ms else 0.0,
+                   "second_gs_pass_rate": round((sp1["gs_reorths"] - sp0["gs_reorths"]) / max(arnoldi, 1), 4),
+                   "mean_j_plus_1": round((sp1["gs_cols"] - sp0["gs_cols"]) / max(arnoldi, 1), 2),
+                   "source": f"CUDA events per kernel class on the library stream over {n_prof} Newton iterations "
+                             f"of the timed trajectory, graphs off"}
+    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in ktimes.items() if v[1]}
+
+    # end to end through the public API with host buffers: the same K
+    # iterations from the same seed, every step uploading the state from
+    # pinned host memory and reading the updated state back
     e2e = None
-    if args.e2e_steps > 0:
-        le = loop  # continue the timed time loop from where it stopped
+    acc_mixed = None
+    if args.e2e:
         pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory().numpy()
+        _reset(g, wl, seed)
+        le = NewtonLoop(g, wl)
         host = [pin(x) for x in g.hf_get_state()[:5]] + [0.0]
+        res = [pin(x) for x in g.hf_get_opening_pressure()[:2]]
         h2d = sum(x.nbytes for x in host[:5])
+        d2h = h2d + sum(x.nbytes for x in res)
+        states = []
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
+        for _ in range(args.steps):
             g.hf_set_state(*host[:5], host[5])
             le.step()
             out = g.hf_get_state()
             for dst, src in zip(host[:5], out[:5]):
                 dst[...] = src
             host[5] = out[5]
+            for dst, src in zip(res, g.hf_get_opening_pressure()[:2]):
+                dst[...] = src
+            if golden is not None:
+                states.append((host[0].copy(), host[1].copy(), res[0].copy()))
         torch.cuda.synchronize(dev)
         te = time.perf_counter() - t0
-        e2e = {"value": args.e2e_steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(h2d), "steps": args.e2e_steps}
+        e2e = {"value": args.steps / te, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "steps": args.steps,
+               "note": "the same Newton iterations as the timed region; every step uploads the state from "
+                       "pinned host memory and reads back the state, the face-node openings and the pressures"}
+        if golden is not None:
+            acc_mixed = accuracy(wl, golden, states)
 
-    # FP64 beside it on the same starting state (fewer steps)
+    # FP64 beside it: the same trajectory, timed, then checked
     fp64 = None
     if args.precision == "mixed" and args.fp64_steps > 0:
         g.hf_set_solver(**solver_kw(args, "fp64"))
-        g.hf_set_state(U, P, al, be)
+        _reset(g, wl, seed)
         l64 = NewtonLoop(g, wl)
         for _ in range(min(args.warmup, 2)):
             l64.step()
-        l64.reports.clear()
+        _reset(g, wl, seed)
+        l64 = NewtonLoop(g, wl)
         torch.cuda.synchronize(dev)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -326,28 +447,19 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         ms64 = e0.elapsed_time(e1)
         fp64 = {"value": args.fp64_steps / (ms64 / 1000.0), "unit": UNIT, "steps": args.fp64_steps,
-                "ms_per_step": ms64 / args.fp64_steps,
+                "ms_per_step": ms64 / args.fp64_steps, "gmres_rtol": args.fp64_rtol,
                 "gmres_iters_per_newton": float(np.mean([r["gmres_iters"] for r in l64.reports])),
                 "restart": args.fp64_restart, "reorth": args.fp64_reorth}
+        if golden is not None:
+            _reset(g, wl, seed)
+            lc = NewtonLoop(g, wl)
+            states = []
+            for _ in range(args.fp64_steps):
+                lc.step()
+                U, P = g.hf_get_state()[:2]
+                states.append((U, P, g.hf_get_opening_pressure()[0]))
+            fp64["accuracy_vs_oracle"] = accuracy(wl, golden, states)
         g.hf_set_solver(**solver_kw(args, prec))
-
-    # roofline of the dominant kernel class, from the events of the timed region
-    elt = 4 if prec == "mixed" else 8
-    algo = algorithmic_bytes(stats, wl.mesh.dim, elt)
-    cand = {k: ktimes[k] for k in ("spmv", "precond")}
-    dom = max(cand, key=lambda k: cand[k][0])
-    kms, kl = cand[dom]
-    peak, peak_src = peaks()
-    achieved = algo[dom] / (kms / kl / 1000.0) / 1e9 if kl else 0.0
-    kname = {"spmv": f"k_spmv<{'float' if elt == 4 else 'double'},3,0>",
-             "precond": f"k_ilu_apply<{'float' if elt == 4 else 'double'},3>"}[dom]
-    roofline = {"bound": "hbm", "kernel": kname, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "peak_source": peak_src,
-                "algorithmic_bytes_per_launch": int(algo[dom]), "launches": kl,
-                "avg_launch_us": 1000.0 * kms / kl if kl else None,
-                "traffic": traffic_from_profiles(kname)}
-    total_ms = sum(v[0] for v in ktimes.values())
-    breakdown = {k: {"ms": round(v[0], 3), "launches": v[1]} for k, v in ktimes.items() if v[1]}
 
     gmres = [r["gmres_iters"] for r in reports]
     out = {
@@ -356,27 +468,30 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f32-inner/f64-refinement" if prec == "mixed" else "f64",
         "data": "synthetic (seeded structured P2 mesh and seed crack)",
         "config": {"workload": wl.name, "dofs": int(g.N), "elements": int(wl.mesh.n_elems),
-                   "precision": prec, "gmres_rtol": 1e-8, "restart": args.restart, "reorth": bool(args.reorth),
+                   "precision": prec, "gmres_rtol": args.rtol, "inner_rtol": 1e-3, "restart": args.restart,
+                   "reorth": args.reorth,
                    "preconditioner": ("block-Jacobi ILU(0) + rigid-body coarse level (%d coarse unknowns)"
-                                      % stats.get("coarse_unknowns", 0)) if args.coarse else "block-Jacobi ILU(0)",
+                                      % st1.get("coarse_unknowns", 0)) if args.coarse else "block-Jacobi ILU(0)",
                    "jacobi_block": args.jacobi_block, "cuda_graphs": bool(args.graphs),
+                   "timed_work": f"Newton iterations 1..{args.steps} of the time loop from the seed state "
+                                 f"(after {args.warmup} untimed iterations of the same loop)",
                    "parallelism": f"replicas x{world}",
-                   "l2": "working set larger than L2 (matrix + factor %.2f GB per replica)" %
-                         (2 * algo["spmv"] / 1e9)},
+                   "l2": "inputs larger than L2 (matrix + factor %.2f GB per replica, L2 129 MB)" %
+                         ((algo["spmv"] + algo["precond"]) / 1e9)},
+        "accuracy_vs_oracle": acc_mixed,
         "fp64": fp64,
         "e2e": e2e,
         "gpu_launches": int(launches),
         "roofline": roofline,
+        "solve_phase": solve_phase,
         "kernel_ms": breakdown,
-        "kernel_timing_source": timing_source,
-        "kernel_ms_total_share_of_step": total_ms / ms if ms else None,
         "gmres_iters_per_newton": float(np.mean(gmres)) if gmres else None,
         "newton_latency_ms": {"p50": 1000 * lat[len(lat) // 2], "p99": 1000 * lat[min(len(lat) - 1, int(0.99 * len(lat)))]}
         if lat else None,
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and args.cpu_baseline:
-        out["cpu_baseline"] = oracle_baseline(wl, args.cpu_budget)
+        out["cpu_baseline"] = oracle_baseline(args.cpu_n)
     g.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -384,43 +499,45 @@ def run_ours(args):
         print(json.dumps(out))
 
 
-def oracle_baseline(wl, budget_s):
-    """The oracle as it stands on the host cores, on a bounded sample of the
-    same workload: the residual and Jacobian terms of a sample of elements and
-    interior facets, scaled to the whole mesh.  The oracle's sparse direct
-    solve cannot run at this size (fill-in), so the figure excludes the linear
-    solve and is an upper bound on the oracle's Newton rate."""
-    from oracle import Oracle, Params
+def accuracy(wl, golden, states):
+    """Per-iteration relative errors (U sample, pressures, face-node openings)
+    of the GPU iterates against the oracle's trajectory of the same loop."""
+    u_idx = np.asarray(golden["u_index"], dtype=np.int64)
+    per = []
+    for rec, (U, P, W) in zip(golden["iters"], states):
+        e = errors_vs_golden(rec, u_idx, U, P, W)
+        per.append({"k": rec["k"], **{k: float("%.3g" % v) for k, v in e.items()}})
+    worst = {k: max(p[k] for p in per) for k in ("U", "P", "w")} if per else None
+    return {"max_rel_err": worst, "per_step": per, "steps_compared": len(per),
+            "oracle": "tests/golden/c3_newton_oracle.json (FP64 oracle trajectory, ILU(0)-GMRES to 1e-13)"}
+
+
+def oracle_baseline(n):
+    """The oracle as it stands on the host cores: one full Newton iteration
+    (assembly summed over a pool of host processes, then the oracle's
+    ILU(0)-GMRES solve to a relative residual of 1e-13) of the penny workload
+    at mesh size n from its seed state.  Reported at that size, not scaled."""
+    from hf_inputs import penny_3d
+    from oracle import Oracle, Params, parallel
+    from oracle.iterative import solve_linear_iterative
+    wl = penny_3d(n=n, crackable="plane", name=f"penny3d_n{n}_plane")
     inj, wts = wl.injection()
-    t0 = time.perf_counter()
     prm = Params(E=wl.E, nu=wl.nu, sigma_c=wl.sigma_c, delta_c=wl.delta_c, b_stab=wl.b_stab, mu=wl.mu, Q0=wl.Q0,
-                 inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=wl.delta_f, dt=wl.dt, L_ref=wl.fluid_length)
+                 inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=wl.delta_f, dt=wl.dt, cutoff_on=True,
+                 L_ref=wl.fluid_length, newton_tol=1e-8)
     o = Oracle(wl.mesh, prm)
-    U, P, al, be = wl.seed()
-    o.set_state(U, P, al, be)
-    t_setup = time.perf_counter() - t0
-    rng = np.random.default_rng(0)
-    interior = np.nonzero(wl.mesh.face_elems[:, 1] >= 0)[0]
-    n_e = n_f = 0
-    t_e = t_f = 0.0
-    deadline = time.perf_counter() + budget_s
-    while time.perf_counter() < deadline:
-        e = int(rng.integers(0, o.ne))
-        t1 = time.perf_counter()
-        o.element_stiffness(e)
-        t_e += time.perf_counter() - t1
-        n_e += 1
-        f = int(interior[rng.integers(0, interior.size)])
-        t1 = time.perf_counter()
-        o.intact_blocks(f)
-        t_f += time.perf_counter() - t1
-        n_f += 1
-    t_full = t_e / n_e * o.ne + t_f / n_f * interior.size
-    return {"value": 1.0 / t_full, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"oracle assembly of {n_e} random elements and {n_f} random interior facets of "
-                      f"{wl.name} ({o.ne} elements, {interior.size} interior facets), scaled to the full "
-                      f"mesh ({t_full:.1f} s per Newton iteration); sparse direct solve excluded "
-                      f"(infeasible at this size), so an upper bound; set-up {t_setup:.1f} s"}
+    o.set_state(*wl.seed())
+    cores = os.cpu_count() or 1
+    info = {}
+    t0 = time.perf_counter()
+    o.newton_step(solve=lambda J, b: solve_linear_iterative(J, b, rtol=1e-13, info=info),
+                  assemble=lambda: parallel.assemble(o, workers=cores))
+    t = time.perf_counter() - t0
+    return {"value": 1.0 / t, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"one full FP64 oracle Newton iteration (assembly over {cores} host processes, "
+                      f"ILU(0)-GMRES to 1e-13 on one core: {info.get('iters')} iterations) of the penny workload "
+                      f"at n = {n} ({o.N} unknowns, {o.ne} elements) from its seed state, {t:.1f} s; "
+                      f"measured at that size, not scaled to the 1.05 M-unknown workload"}
 
 
 def _solver_for_requests(args, tuner=None):
@@ -544,18 +661,27 @@ def run_sweep(args):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle itself, one full Newton iteration
+    of the penny workload per step at a size that keeps the whole run within
+    a few minutes (stated in the line)."""
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    wl = workload(args.config)
-    base = oracle_baseline(wl, args.cpu_budget)
-    out = {"metric": METRIC, "value": base["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1000.0 / base["value"], "higher_is_better": True,
+    for _ in range(args.warmup):
+        oracle_baseline(args.cpu_n)
+    vals = [oracle_baseline(args.cpu_n) for _ in range(args.ref_steps)]
+    base = vals[-1]
+    value = len(vals) / sum(1.0 / v["value"] for v in vals)
+    base["value"] = value
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": len(vals),
+           "warmup": args.warmup, "ms_per_step": 1000.0 / value, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "impl": "reference",
            "data": "synthetic (seeded structured P2 mesh and seed crack)",
-           "config": {"workload": wl.name, "precision": "fp64 oracle"},
+           "config": {"workload": workload(args.config).name, "precision": "fp64 oracle",
+                      "oracle_workload": f"penny n = {args.cpu_n} (a bounded sample: the 1.05 M-unknown workload "
+                                         f"takes the oracle over 10 minutes per Newton iteration)"},
            "cpu_baseline": base,
-           "e2e": {"value": base["value"], "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+           "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
 
@@ -568,16 +694,20 @@ def main():
     ap.add_argument("--config", default="c3")
     ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
     ap.add_argument("--jacobi-block", dest="jacobi_block", type=int, default=32)
-    ap.add_argument("--restart", type=int, default=60)
-    ap.add_argument("--reorth", type=int, default=1)
-    ap.add_argument("--fp64-restart", dest="fp64_restart", type=int, default=60)
-    ap.add_argument("--fp64-reorth", dest="fp64_reorth", type=int, default=0)
+    ap.add_argument("--restart", type=int, default=HEADLINE["mixed"]["restart"])
+    ap.add_argument("--reorth", type=int, default=HEADLINE["mixed"]["reorth"])
+    ap.add_argument("--fp64-restart", dest="fp64_restart", type=int, default=HEADLINE["fp64"]["restart"])
+    ap.add_argument("--fp64-reorth", dest="fp64_reorth", type=int, default=HEADLINE["fp64"]["reorth"])
     ap.add_argument("--max-iters", dest="max_iters", type=int, default=8000)
     ap.add_argument("--coarse", type=int, default=1)
     ap.add_argument("--graphs", type=int, default=1)
-    ap.add_argument("--fp64-steps", dest="fp64_steps", type=int, default=3)
-    ap.add_argument("--e2e-steps", dest="e2e_steps", type=int, default=4)
-    ap.add_argument("--cpu-budget", dest="cpu_budget", type=float, default=15.0)
+    ap.add_argument("--fp64-steps", dest="fp64_steps", type=int, default=-1, help="-1: as many as --steps")
+    ap.add_argument("--e2e", type=int, default=1)
+    ap.add_argument("--rtol", type=float, default=HEADLINE["mixed"]["rtol"],
+                    help="GMRES relative residual of the mixed path")
+    ap.add_argument("--fp64-rtol", dest="fp64_rtol", type=float, default=HEADLINE["fp64"]["rtol"])
+    ap.add_argument("--cpu-n", dest="cpu_n", type=int, default=6, help="penny mesh size of the oracle baseline")
+    ap.add_argument("--ref-steps", dest="ref_steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--mode", default="newton", choices=["newton", "serve", "sweep"])
     ap.add_argument("--slots", type=int, default=8)
@@ -590,6 +720,8 @@ def main():
     ap.add_argument("--verbose", type=int, default=0)
     ap.add_argument("--request-max-iters", dest="request_max_iters", type=int, default=3000)
     args = ap.parse_args()
+    if args.fp64_steps < 0:
+        args.fp64_steps = args.steps
     if args.impl == "reference":
         run_reference(args)
     elif args.mode == "serve":

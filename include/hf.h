@@ -90,6 +90,7 @@ typedef struct {
 
 /* Solver options.  Defaults come from hf_default_solver_opts. */
 enum { HF_PREC_FP64 = 0, HF_PREC_MIXED = 1 };
+enum { HF_SCHEME_COUPLED = 0, HF_SCHEME_STAGGERED = 1 };
 typedef struct {
   int precision;        /* HF_PREC_FP64 or HF_PREC_MIXED (FP32 SpMV/ILU in FP64 IR) */
   int restart;          /* GMRES restart length m (1..96; default 60) */
@@ -102,9 +103,14 @@ typedef struct {
   int use_graphs;       /* 1: capture each GMRES cycle in a CUDA graph */
   int coarse;           /* 1: add the rigid-body coarse correction to the preconditioner */
   int coarse_max;       /* bound on the coarse unknowns (16..4096): sets the aggregate size */
-  int reorth;           /* classical Gram-Schmidt passes: 0 one; 1 (default) a second,
-                           re-orthogonalising pass when the first removed more than 30% of the
-                           vector; 2 always two.  FP32 cycles lose orthogonality with one */
+  int reorth;           /* classical Gram-Schmidt passes: 0 one; 1 a second, re-orthogonalising
+                           pass when the first removed more than 30% of the vector; 2 always
+                           two; 3 (default) two, the second delayed by one Arnoldi step and fused
+                           with the next step's first (two basis sweeps and one global reduction
+                           per step).  FP32 cycles lose orthogonality with one */
+  int scheme;           /* HF_SCHEME_COUPLED (default): one Newton iteration of the fully-coupled
+                           system; HF_SCHEME_STAGGERED: one iteration of the staggered scheme of
+                           Sec. 4.3 (FP64 only) */
 } hf_solver_opts;
 
 /* Report of one Newton iteration (Sec. 3: convergence on the Euclidean norms
@@ -159,8 +165,23 @@ hf_status hf_get_state(hf_mesh* h, double* U, double* P, int8_t* alpha, int8_t* 
 
 /* One Newton iteration of Sec. 3 (assemble R and J, solve J d = -R, update).
  * Returns HF_OK even if the iteration did not converge (see rep->converged);
- * HF_ERR_NONFINITE if a norm is not finite (state then unchanged). */
+ * HF_ERR_NONFINITE if a norm is not finite (state then unchanged).
+ * With scheme HF_SCHEME_STAGGERED it is instead one iteration of the
+ * staggered scheme of Sec. 4.3 ("Fully-coupled vs. staggered"): the
+ * mechanical equation solved for U with the pressure of the previous
+ * iteration, A dU = -R_u(U, P), then the lubrication equation for P at the
+ * updated opening, D dP = -R_p(U + dU, P) (A, D the diagonal blocks of Eq.
+ * fully-coupled-fully-discrete); du_rel and dp_rel are those two increments.
+ * The decoupled fluid problem is elliptic and needs an essential pressure
+ * (hf_set_fixed_pressure). */
 hf_status hf_newton_step(hf_mesh* h, hf_newton_report* rep);
+
+/* Essential pressure condition (Sec. 4.3: the decoupled fluid equation of
+ * the staggered scheme needs the pressure given at least at one point):
+ * pressure DOF p_dofs[i] is held at values[i] by an identity row, in both
+ * schemes.  Replaces any earlier set; n = 0 clears it.  HF_ERR_INVALID_ARG
+ * on a DOF out of range or a non-finite value. */
+hf_status hf_set_fixed_pressure(hf_mesh* h, int64_t n, const int64_t* p_dofs, const double* values);
 
 /* Fracture criterion (Sec. 3, activation of the TSL): on crackable intact
  * facets, alpha := 1 where the normal DG traction n.<sigma>n + (b/h)(lambda +
@@ -213,7 +234,10 @@ hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
  * process so far, [9] CUDA error met when reading timing events recorded
  * inside a captured GMRES cycle (0: none; graph cycles then go untimed),
  * [10] device bytes the handle holds, [11] coarse unknowns in use (0: one
- * level), [12] elements per coarse aggregate, [13..15] zero.  st holds 16. */
+ * level), [12] elements per coarse aggregate, [13] second Gram-Schmidt passes
+ * taken by GMRES since the handle was created, [14] basis vectors swept by
+ * first Gram-Schmidt passes (the sum of j + 1 over Arnoldi steps j), [15] basis
+ * vectors swept by second passes.  st holds 16. */
 hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
 
 const char* hf_last_error(const hf_mesh* h);
@@ -234,7 +258,10 @@ const char* hf_last_error(const hf_mesh* h);
  * partial sums of at most 4096 blocks of 16,384 unknowns); larger sizes,
  * negative sizes and null pointers return HF_ERR_INVALID_ARG.  The first call
  * on each device looks up the scratch address with the device current (make
- * that first call before any stream capture).  Every call shares the one
+ * that first call before any stream capture); every later call whose stream
+ * is not being captured looks it up again, so an address cached before a
+ * device reset is not reused (a call inside a capture uses the address of the
+ * last call made outside one).  Every call shares the one
  * scratch array and clears its counter first, so calls that overlap on the
  * GPU (different streams, or host threads racing) give wrong results.  err
  * (may be NULL) receives a message of at most err_len bytes. */

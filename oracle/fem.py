@@ -222,6 +222,8 @@ class Params:
     L_ref: float = 100.0
     newton_tol: float = 1e-10
     newton_maxit: int = 25
+    fixed_pdofs: tuple = ()        # pressure DOFs held at fixed_pvals (an essential condition)
+    fixed_pvals: tuple = ()
 
 
 class Oracle:
@@ -580,11 +582,17 @@ class Oracle:
         # injection (point source Q0 split by weights)
         for g, wgt in zip(p.inj_pdofs, p.inj_weights):
             R[self.Nu + g] -= c * p.Q0 * wgt
-        # identity rows: inactive pressures (p = p_v) and Dirichlet displacements
-        ident = list(self.Nu + np.nonzero(~act)[0]) + list(self.m.dir_dof)
+        # identity rows: inactive pressures (p = p_v), fixed pressures and
+        # Dirichlet displacements
+        fixed = np.zeros(self.Np, dtype=bool)
+        fixed[list(p.fixed_pdofs)] = True
+        fval = np.full(self.Np, p.p_vapor)
+        fval[list(p.fixed_pdofs)] = p.fixed_pvals
+        free = ~act & ~fixed
+        ident = list(self.Nu + np.nonzero(free)[0]) + list(self.Nu + np.nonzero(fixed)[0]) + list(self.m.dir_dof)
         ident = np.asarray(ident, dtype=np.int64)
-        target = np.concatenate([np.full(int((~act).sum()), p.p_vapor), self.m.dir_val])
-        cur = np.concatenate([P[~act], U[self.m.dir_dof]])
+        target = np.concatenate([np.full(int(free.sum()), p.p_vapor), fval[fixed], self.m.dir_val])
+        cur = np.concatenate([P[free], P[fixed], U[self.m.dir_dof]])
         R[ident] = cur - target
         if J is not None and ident.size:
             # row r of J becomes e_r^T: keep the other rows, add the unit diagonal
@@ -630,6 +638,39 @@ class Oracle:
             self.P[act] = np.maximum(self.P[act], self.prm.p_vapor)
             # the increment of the nodal pressure array is the change applied,
             # cut-off included
+            dP = self.P - P_old
+        du = np.linalg.norm(dU) / max(np.linalg.norm(self.U), 1e-300)
+        dp = np.linalg.norm(dP) / max(np.linalg.norm(self.P), 1e-300)
+        return dict(du_rel=du, dp_rel=dp, res_norm=float(np.linalg.norm(R)),
+                    converged=bool(du <= self.prm.newton_tol and dp <= self.prm.newton_tol))
+
+    def staggered_step(self, solve=None):
+        """One iteration of the staggered scheme of Sec. 4.3 ("Fully-coupled
+        vs. staggered"): the two equations solved in turn for their own
+        unknown with the other taken from the previous iteration, i.e. the
+        linear system of Eq. fully-coupled-fully-discrete decoupled into
+        A dU = -R_u(U, P) and then, at the updated opening,
+        D dP = -R_p(U + dU, P).  The decoupled fluid problem is elliptic and
+        needs an essential pressure somewhere (Params.fixed_pdofs).  Reports
+        the relative increments as newton_step does."""
+        solve = solve or self.solve_linear
+        Nu = self.Nu
+        R, J = self.assemble()
+        dU = solve(J[:Nu, :Nu].tocsr(), -R[:Nu])
+        self.U = self.U + dU
+        R2, J2 = self.assemble()
+        D = J2[Nu:, Nu:].tocsr()
+        if np.any(abs(D).max(axis=1).toarray().ravel() == 0.0):
+            # a pressure row with no conductivity left (the opening closed on
+            # every facet around it): the decoupled fluid problem is singular
+            nan = float("nan")
+            return dict(du_rel=nan, dp_rel=nan, res_norm=float(np.linalg.norm(R)), converged=False)
+        dP = solve(D, -R2[Nu:])
+        P_old = self.P
+        self.P = self.P + dP
+        if self.prm.cutoff_on:
+            act = self.active_pdofs()
+            self.P[act] = np.maximum(self.P[act], self.prm.p_vapor)
             dP = self.P - P_old
         du = np.linalg.norm(dU) / max(np.linalg.norm(self.U), 1e-300)
         dp = np.linalg.norm(dP) / max(np.linalg.norm(self.P), 1e-300)

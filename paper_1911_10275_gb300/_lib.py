@@ -13,6 +13,8 @@ from . import build as _build
 HF_OK = 0
 HF_PREC_FP64 = 0
 HF_PREC_MIXED = 1
+HF_SCHEME_COUPLED = 0
+HF_SCHEME_STAGGERED = 1
 STATUS = {0: "HF_OK", -1: "HF_ERR_INVALID_ARG", -2: "HF_ERR_OOM", -3: "HF_ERR_CUDA",
           -4: "HF_ERR_NOT_CONVERGED", -5: "HF_ERR_NONFINITE", -6: "HF_ERR_TIMEOUT",
           -7: "HF_ERR_DEVICE_ASSERT", -8: "HF_ERR_STATE"}
@@ -35,7 +37,7 @@ class hf_solver_opts(C.Structure):
     _fields_ = [("precision", C.c_int), ("restart", C.c_int), ("max_iters", C.c_int),
                 ("rtol", C.c_double), ("inner_rtol", C.c_double), ("jacobi_block", C.c_int),
                 ("fluid_scaling", C.c_int), ("newton_tol", C.c_double), ("use_graphs", C.c_int),
-                ("coarse", C.c_int), ("coarse_max", C.c_int), ("reorth", C.c_int)]
+                ("coarse", C.c_int), ("coarse_max", C.c_int), ("reorth", C.c_int), ("scheme", C.c_int)]
 
 
 class hf_newton_report(C.Structure):
@@ -95,6 +97,7 @@ SIGNATURES = {
     "hf_set_injection": (C.c_int, [_H, C.c_double, C.c_double, C.c_int64, _i64p, _dp, C.c_double,
                                    C.c_double, C.c_double, C.c_int, C.c_double]),
     "hf_set_solver": (C.c_int, [_H, C.POINTER(hf_solver_opts)]),
+    "hf_set_fixed_pressure": (C.c_int, [_H, C.c_int64, _i64p, _dp]),
     "hf_set_state": (C.c_int, [_H, _dp, _dp, _i8p, _i8p, _dp, C.c_double]),
     "hf_get_state": (C.c_int, [_H, _dp, _dp, _i8p, _i8p, _dp, _dp]),
     "hf_newton_step": (C.c_int, [_H, C.POINTER(hf_newton_report)]),
@@ -216,6 +219,8 @@ def solver_opts(**kw):
     for k, v in kw.items():
         if k == "precision" and isinstance(v, str):
             v = HF_PREC_MIXED if v == "mixed" else HF_PREC_FP64
+        if k == "scheme" and isinstance(v, str):
+            v = {"coupled": HF_SCHEME_COUPLED, "staggered": HF_SCHEME_STAGGERED}[v]
         setattr(o, k, v)
     return o
 
@@ -285,6 +290,11 @@ class HFMesh:
         o = hf_solver_opts()
         self.lib.hf_default_solver_opts(C.byref(o))
         return o
+
+    def hf_set_fixed_pressure(self, p_dofs, values):
+        d = np.ascontiguousarray(p_dofs, dtype=np.int64)
+        v = np.ascontiguousarray(values, dtype=np.float64)
+        self._check(self.lib.hf_set_fixed_pressure(self.h, int(d.size), _ptr(d, C.c_int64), _ptr(v, C.c_double)))
 
     def hf_set_solver(self, **kw):
         o = solver_opts(**kw)
@@ -399,7 +409,7 @@ class HFMesh:
         self._check(self.lib.hf_get_stats(self.h, _ptr(st, C.c_int64)))
         keys = ["elements", "interior_slots", "subdomain_slots", "levels_max", "subdomains", "nl_faces",
                 "n_p", "faces", "kernel_launches", "graph_timing_error", "device_bytes", "coarse_unknowns",
-                "aggregate_size"]
+                "aggregate_size", "gs_reorths", "gs_cols", "gs_reorth_cols"]
         return dict(zip(keys, (int(x) for x in st)))
 
     def hf_solve_linear(self, rhs):

@@ -481,7 +481,8 @@ void hf_default_solver_opts(hf_solver_opts* o) {
   o->use_graphs = 0;
   o->coarse = 1;
   o->coarse_max = 2048;
-  o->reorth = 1;
+  o->reorth = 3;
+  o->scheme = HF_SCHEME_COUPLED;
 }
 
 const char* hf_last_error(const hf_mesh* h) { return h ? h->err.c_str() : "null handle"; }
@@ -502,6 +503,9 @@ hf_status hf_mesh_destroy(hf_mesh* h) {
     if (h->prof.ev[i]) cudaEventDestroy(h->prof.ev[i]);
   for (const hf_mesh::Alloc& a : h->allocs) cudaFreeAsync(a.raw, h->stream);
   if (h->stream) cudaStreamSynchronize(h->stream);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
+  if (h->side) cudaStreamDestroy(h->side);
   if (h->own_stream && h->stream) cudaStreamDestroy(h->stream);
   delete h;
   return HF_OK;
@@ -538,6 +542,10 @@ hf_status hf_mesh_create(const hf_mesh_desc* desc, void* cuda_stream, hf_mesh** 
       return fail(HF_ERR_CUDA, "cudaStreamCreate");
     h->own_stream = true;
   }
+  if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess)
+    return fail(HF_ERR_CUDA, "side stream of the preconditioner");
   // validate element nodes
   for (long long i = 0; i < (long long)ne * nen; ++i)
     if (desc->elem_nodes[i] < 0 || desc->elem_nodes[i] >= desc->n_nodes) return fail(HF_ERR_INVALID_ARG, "elem_nodes out of range");
@@ -723,6 +731,9 @@ hf_status hf_mesh_create(const hf_mesh_desc* desc, void* cuda_stream, hf_mesh** 
   d.pinc_a = upload(h, pinc_a);
   d.p_active = dzeros<signed char>(h, np);
   d.inj_w = dzeros<double>(h, np);
+  d.p_fixval = upload(h, std::vector<double>(std::max<size_t>(np, 1), std::nan("")));
+  d.sinv_d = dzeros<double>(h, np);
+  d.phase = 0;
   d.ubar = upload(h, ubar);
   d.fext = dzeros<double>(h, h->nu);
   d.scal = dzeros<double>(h, 16);
@@ -744,7 +755,7 @@ hf_status hf_mesh_create(const hf_mesh_desc* desc, void* cuda_stream, hf_mesh** 
   if (!d.xyz || !d.enode || !d.grad_lam || !d.vol || !d.nbr || !d.slot_face || !d.slot_side || !d.dirmask ||
       !d.nlmask || !d.fe || !d.fl || !d.fnormal || !d.farea || !d.fh || !d.fsg || !d.loc_m || !d.loc_p ||
       !d.fpdof || !d.crack || !d.alpha || !d.beta || !d.w_old || !d.nl || !d.pinc_ptr || !d.pinc_face ||
-      !d.pinc_a || !d.p_active || !d.inj_w || !d.ubar || !d.fext || !d.scal || !d.err_flag || !h->fneu_trac || !h->fneu ||
+      !d.pinc_a || !d.p_active || !d.inj_w || !d.p_fixval || !d.sinv_d || !d.ubar || !d.fext || !d.scal || !d.err_flag || !h->fneu_trac || !h->fneu ||
       !h->J64.dg || !h->X || !h->R || !h->D || !h->tmp64 || !h->r64 || !h->d_elist || !h->d_count ||
       !h->d_red || !h->d_wtmp)
     return fail(HF_ERR_OOM, "device allocation failed");
@@ -825,7 +836,9 @@ hf_status hf_set_solver(hf_mesh* h, const hf_solver_opts* o) {
   HF_GUARD(h);
   if (!o || (o->precision != HF_PREC_FP64 && o->precision != HF_PREC_MIXED) || o->restart < 1 || o->restart > GM_MAX ||
       o->max_iters < 0 || !(o->rtol > 0) || !(o->inner_rtol > 0) || o->jacobi_block < 1 || o->coarse < 0 ||
-      o->coarse > 1 || o->coarse_max < 16 || o->coarse_max > 4096 || o->reorth < 0 || o->reorth > 2)
+      o->coarse > 1 || o->coarse_max < 16 || o->coarse_max > 4096 || o->reorth < 0 || o->reorth > 3 ||
+      (o->scheme != HF_SCHEME_COUPLED && o->scheme != HF_SCHEME_STAGGERED) ||
+      (o->scheme == HF_SCHEME_STAGGERED && o->precision != HF_PREC_FP64))
     return set_error(h, HF_ERR_INVALID_ARG, "solver options out of range");
   bool regroup = std::min(256, o->jacobi_block) != h->G;
   bool rescale = o->fluid_scaling != h->opts.fluid_scaling;
@@ -917,9 +930,65 @@ static hf_status assemble_nl(hf_mesh* h) {
   return check_cuda(h, cudaGetLastError(), "face_nl");
 }
 
+// One iteration of the staggered scheme (Sec. 4.3): the mechanical equation
+// solved for U with the pressure of the previous iteration, A dU = -R_u(U, P),
+// then the lubrication equation for P at the new opening, D dP =
+// -R_p(U + dU, P).  Both solves use the GMRES of the coupled system with the
+// other block's rows turned into identity rows (DevMesh::phase).
+static hf_status staggered_step(hf_mesh* h, hf_newton_report* rep) {
+  hf_newton_report r{}, r1{}, r2{};
+  hf_status s;
+  double n1[4], n2[4];
+  if ((s = assemble_nl(h))) return s;
+  residual(h, h->X, h->R);
+  r.res_norm = sqrt(device_norm2(h, h->R, h->N));
+  if (!std::isfinite(r.res_norm)) return set_error(h, HF_ERR_NONFINITE, "residual is not finite");
+  if ((s = refactor(h))) return s;
+  launch_neg_part(h, h->R, h->K64.b, 1, 0);
+  h->d.phase = 1;
+  s = linear_solve(h, h->K64.b, h->D, &r1);
+  h->d.phase = 0;
+  if (s) return s;
+  if ((s = newton_update(h, h->D, n1))) return s;
+  if ((s = assemble_nl(h))) return s;
+  residual(h, h->X, h->R);
+  launch_neg_part(h, h->R, h->K64.b, 0, 1);
+  launch_diag_d(h);
+  h->d.phase = 2;
+  s = linear_solve(h, h->K64.b, h->D, &r2);
+  h->d.phase = 0;
+  if (s) return s;
+  if ((s = newton_update(h, h->D, n2))) return s;
+  r.du_rel = sqrt(n1[0]) / std::max(sqrt(n1[1]), 1e-300);
+  r.dp_rel = h->np ? sqrt(n2[2]) / std::max(sqrt(n2[3]), 1e-300) : 0.0;
+  r.gmres_iters = r1.gmres_iters + r2.gmres_iters;
+  r.lin_res = std::max(r1.lin_res, r2.lin_res);
+  r.lin_converged = r1.lin_converged && r2.lin_converged;
+  if (!std::isfinite(r.du_rel) || !std::isfinite(r.dp_rel)) return set_error(h, HF_ERR_NONFINITE, "update is not finite");
+  r.converged = r.du_rel <= h->opts.newton_tol && r.dp_rel <= h->opts.newton_tol;
+  if (rep) *rep = r;
+  return HF_OK;
+}
+
+hf_status hf_set_fixed_pressure(hf_mesh* h, int64_t n, const int64_t* p_dofs, const double* values) {
+  HF_GUARD(h);
+  if (n < 0 || (n > 0 && (!p_dofs || !values))) return set_error(h, HF_ERR_INVALID_ARG, "null fixed-pressure arrays");
+  std::vector<double> v(std::max<long long>(h->np, 1), std::nan(""));
+  for (int64_t i = 0; i < n; ++i) {
+    if (p_dofs[i] < 0 || p_dofs[i] >= h->np) return set_error(h, HF_ERR_INVALID_ARG, "fixed pressure dof out of range");
+    if (!std::isfinite(values[i])) return set_error(h, HF_ERR_INVALID_ARG, "fixed pressure value not finite");
+    v[p_dofs[i]] = values[i];
+  }
+  HF_CUDA(h, cudaMemcpyAsync(h->d.p_fixval, v.data(), v.size() * sizeof(double), cudaMemcpyHostToDevice, h->stream));
+  h->sd_dirty = all_subdomains(h);
+  invalidate_graphs(h);
+  return check_cuda(h, cudaStreamSynchronize(h->stream), "set_fixed_pressure");
+}
+
 hf_status hf_newton_step(hf_mesh* h, hf_newton_report* rep) {
   HF_GUARD(h);
   if (!h->material_set || !h->injection_set) return set_error(h, HF_ERR_STATE, "set material and injection first");
+  if (h->opts.scheme == HF_SCHEME_STAGGERED) return staggered_step(h, rep);
   hf_newton_report r{};
   hf_status s;
   if ((s = assemble_nl(h))) return s;
@@ -1178,7 +1247,9 @@ hf_status hf_get_stats(const hf_mesh* h, int64_t* st) {
   st[10] = h->bytes_allocated;
   st[11] = h->opts.coarse ? h->nc : 0;
   st[12] = h->agg_size;
-  for (int i = 13; i < 16; ++i) st[i] = 0;
+  st[13] = h->gs_reorths;
+  st[14] = h->gs_cols;
+  st[15] = h->gs_reorth_cols;
   return HF_OK;
 }
 
@@ -1367,7 +1438,10 @@ hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, const hf_solver_opt
   add(ldv * (mres + 1) * 8); for (int i = 0; i < 5; ++i) add(N * 8);
   add(ldv * (mres + 1) * 4); for (int i = 0; i < 5; ++i) add(N * 4);
   add(ne * lus * 8); add(ne * lus * 4); add(std::max(np, 1LL) * 8); add(std::max(np, 1LL) * 4);
-  add(nmat * 4); add(152 * 4 * GM_LD * 8); add((long long)sizeof(GmresState));
+  add(nmat * 4); add((long long)std::max(152 * 4 * GM_LD, GS_MAXB_HOST * (2 * GM_MAX + 2)) * 8);
+  add(GS_MAXB_HOST * 8);
+  add(std::max<long long>(np, 1) * 8); add(std::max<long long>(np, 1) * 8);  // fixed pressures, fluid diagonal
+  add((long long)sizeof(GmresState));
   // coarse level (largest layout the options allow: coarse_max = 4096 at most)
   {
     int cA = 0, cnagg = 0, cnc = 0;

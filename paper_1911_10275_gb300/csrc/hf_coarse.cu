@@ -436,12 +436,12 @@ template <> const double* coarse_coords<double>(const hf_mesh* h) { return h->rc
 template <> const float* coarse_coords<float>(const hf_mesh* h) { return h->rc32; }
 
 template <typename T, int DIM>
-void coarse_pre(hf_mesh* h, const Krylov<T>& K, const T* rin, const int* skip) {
+void coarse_pre(hf_mesh* h, const Krylov<T>& K, const T* rin, const int* skip, cudaStream_t st) {
   note_launch();
-  k_coarse_restrict<T, DIM><<<h->nagg, RESTRICT_THREADS, 0, h->stream>>>(h->d, h->agg_size, coarse_coords<T>(h), rin,
-                                                                           K.cc, skip);
+  k_coarse_restrict<T, DIM><<<h->nagg, RESTRICT_THREADS, 0, st>>>(h->d, h->agg_size, coarse_coords<T>(h), rin,
+                                                                    K.cc, skip);
   note_launch();
-  k_coarse_gemv<T><<<(h->nc + 7) / 8, 256, 0, h->stream>>>(coarse_inverse<T>(h), h->nc, K.cc, K.cy, skip);
+  k_coarse_gemv<T><<<(h->nc + 7) / 8, 256, 0, st>>>(coarse_inverse<T>(h), h->nc, K.cc, K.cy, skip);
 }
 
 template <typename T, int DIM> void coarse_post(hf_mesh* h, const Krylov<T>& K, T* z, const int* skip) {
@@ -451,10 +451,10 @@ template <typename T, int DIM> void coarse_post(hf_mesh* h, const Krylov<T>& K, 
                                                                                coarse_coords<T>(h), K.cy, z, skip);
 }
 
-template void coarse_pre<float, 2>(hf_mesh*, const Krylov<float>&, const float*, const int*);
-template void coarse_pre<float, 3>(hf_mesh*, const Krylov<float>&, const float*, const int*);
-template void coarse_pre<double, 2>(hf_mesh*, const Krylov<double>&, const double*, const int*);
-template void coarse_pre<double, 3>(hf_mesh*, const Krylov<double>&, const double*, const int*);
+template void coarse_pre<float, 2>(hf_mesh*, const Krylov<float>&, const float*, const int*, cudaStream_t);
+template void coarse_pre<float, 3>(hf_mesh*, const Krylov<float>&, const float*, const int*, cudaStream_t);
+template void coarse_pre<double, 2>(hf_mesh*, const Krylov<double>&, const double*, const int*, cudaStream_t);
+template void coarse_pre<double, 3>(hf_mesh*, const Krylov<double>&, const double*, const int*, cudaStream_t);
 template void coarse_post<float, 2>(hf_mesh*, const Krylov<float>&, float*, const int*);
 template void coarse_post<float, 3>(hf_mesh*, const Krylov<float>&, float*, const int*);
 template void coarse_post<double, 2>(hf_mesh*, const Krylov<double>&, double*, const int*);

@@ -139,6 +139,9 @@ struct DevMesh {
   signed char* pinc_a;      // face-node index of the pressure node in that facet
   signed char* p_active;    // [np] touches a facet with beta = 1
   double* inj_w;            // [np] injection weights
+  double* p_fixval;         // [np] value of an essential (fixed) pressure, NaN where free
+  double* sinv_d;           // [np] fluid-only solves: inverse diagonal of the pressure block
+  int phase;                // 0 coupled; staggered scheme: 1 mechanics only, 2 fluid only
   // boundary data
   double* ubar;             // [nu] Dirichlet values (0 elsewhere)
   double* fext;             // [nu] Neumann load vector

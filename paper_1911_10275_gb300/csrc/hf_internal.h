@@ -51,6 +51,8 @@ template <typename T> struct Krylov {
 // longest GMRES cycle, and the leading dimension of its Hessenberg matrix
 constexpr int GM_MAX = 96;
 constexpr int GM_LD = GM_MAX + 1;
+// largest grid of the Gram-Schmidt kernels (rows of their partial tables)
+constexpr int GS_MAXB_HOST = 256;
 
 // device scalars of the GMRES driver (one record, double precision); the
 // host reads back only the leading scalars
@@ -63,11 +65,15 @@ struct GmresState {
   int jlast;
   int iters;
   int skip2;             // 1: the second Gram-Schmidt pass of this step is not needed
+  int reorths;           // second Gram-Schmidt passes taken (running count)
+  int pad_;
+  long long reorth_cols; // basis columns swept by those second passes (running count)
   double g[GM_LD];
   double h2[GM_LD];      // second Gram-Schmidt pass coefficients
   double cs[GM_MAX], sn[GM_MAX];
   double y[GM_MAX];
   double H[GM_LD * GM_MAX];  // Hessenberg, rotated in place (column-major, ld GM_LD)
+  double Hr[GM_LD * GM_MAX]; // delayed CGS2: the Hessenberg matrix before rotation
 };
 
 // event-timed kernel classes (profiling mode)
@@ -102,6 +108,10 @@ struct hf_mesh {
   long long ne = 0, nf = 0, nnodes = 0, nu = 0, np = 0, N = 0;
   cudaStream_t stream = nullptr;
   bool own_stream = false;
+  // side stream of the preconditioner: the coarse restriction and solve run
+  // on it beside the ILU(0) apply (a fork/join that graph capture keeps)
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   std::string err;
   bool poisoned = false;
   bool material_set = false, injection_set = false;
@@ -144,6 +154,11 @@ struct hf_mesh {
   int* d_sdlist = nullptr;     // subdomain list scratch
   int* d_count = nullptr;      // counters [0]: criterion, [1]: accept, [2..]: reduction counters
   double* d_partial = nullptr; // block partials of reductions
+  double* d_part2 = nullptr;   // block partials of the Gram-Schmidt norms (one per CTA)
+  int gs_blocks = 0;           // CTAs of the Gram-Schmidt kernels (one per SM)
+  long long gs_reorths = 0;    // second Gram-Schmidt passes taken since the workspace was made
+  long long gs_reorth_cols = 0; // basis columns those passes swept
+  long long gs_cols = 0;       // basis columns swept by first passes: sum over Arnoldi steps of j + 1
   double* d_red = nullptr;     // reduction results
   double* d_wtmp = nullptr;    // facet opening scratch / criterion output
   hfk::GmresState* d_gs = nullptr;
@@ -197,7 +212,8 @@ void coarse_sizes(long long ne, int dim, int coarse_max, int* A, int* nagg, int*
 hf_status coarse_layout(hf_mesh* h);
 hf_status coarse_refactor(hf_mesh* h);
 hf_status coarse_rebuild_copy(hf_mesh* h, double* A0_host, double* inv_host, double* geo_host);
-template <typename T, int DIM> void coarse_pre(hf_mesh* h, const Krylov<T>& K, const T* rin, const int* skip);
+template <typename T, int DIM>
+void coarse_pre(hf_mesh* h, const Krylov<T>& K, const T* rin, const int* skip, cudaStream_t st);
 template <typename T, int DIM> void coarse_post(hf_mesh* h, const Krylov<T>& K, T* z, const int* skip);
 // solver side (hf_solve.cu)
 hf_status solver_alloc(hf_mesh* h);
@@ -208,6 +224,8 @@ hf_status residual(hf_mesh* h, const double* X, double* R);
 hf_status apply_jacobian(hf_mesh* h, const double* x, double* y);
 hf_status linear_solve(hf_mesh* h, const double* b, double* x, hf_newton_report* rep);
 hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]);
+void launch_neg_part(hf_mesh* h, const double* R, double* b, int keep_u, int keep_p);
+void launch_diag_d(hf_mesh* h);
 double device_norm2(hf_mesh* h, const double* v, long long n);
 hf_status set_error(hf_mesh* h, hf_status s, const std::string& msg);
 hf_status check_cuda(hf_mesh* h, cudaError_t e, const char* where);

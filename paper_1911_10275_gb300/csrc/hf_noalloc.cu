@@ -109,15 +109,25 @@ extern "C" hf_status hf_increment_norms_noalloc(const double* d_dx, const double
     set_msg(err, err_len, "hf_increment_norms_noalloc: no usable current device");
     return HF_ERR_CUDA;
   }
-  // one-time set-up per device: the device address of the static scratch
+  // the device address of the static scratch: looked up on the first call on
+  // each device, and again on every call whose stream is not being captured,
+  // so that an address cached before a device reset (which reloads the
+  // library's device module) is never used; a call inside a stream capture
+  // uses the address of the last call made outside one
   double* sc = nullptr;
   {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    const cudaError_t qe = cudaStreamIsCapturing(st, &cs);
+    if (qe != cudaSuccess) cudaGetLastError();  // the query's own error is not sticky; keep it out of later checks
+    const bool capturing = qe != cudaSuccess || cs != cudaStreamCaptureStatusNone;
     std::lock_guard<std::mutex> g(na_mutex);
-    if (!na_ptr[dev]) {
+    if (!na_ptr[dev] || !capturing) {
       void* p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, na_scratch);
+      cudaError_t e = capturing ? cudaErrorStreamCaptureUnsupported : cudaGetSymbolAddress(&p, na_scratch);
       if (e != cudaSuccess || !p) {
-        set_msg(err, err_len, "hf_increment_norms_noalloc: cudaGetSymbolAddress failed");
+        set_msg(err, err_len,
+                capturing ? "hf_increment_norms_noalloc: first call on this device made during stream capture"
+                          : "hf_increment_norms_noalloc: cudaGetSymbolAddress failed");
         return HF_ERR_CUDA;
       }
       na_ptr[dev] = static_cast<double*>(p);

@@ -116,7 +116,12 @@ __device__ void pressure_row(const DevMesh& m, int g, const T* __restrict__ x, T
   using L = NL<DIM>;
   constexpr int F = S::nfn, NED = S::ned;
   double c = m.scal[0];
-  if (!m.p_active[g]) {
+  const double fv = m.p_fixval[g];
+  if (fv == fv) {  // an essential pressure: identity row p = fv
+    y[m.nu + g] = (MODE == 0) ? x[m.nu + g] : (T)((double)x[m.nu + g] - fv);
+    return;
+  }
+  if (!m.p_active[g] || (MODE == 0 && m.phase == 1)) {
     y[m.nu + g] = (MODE == 0) ? x[m.nu + g] : (T)((double)x[m.nu + g] - m.p_v);
     return;
   }
@@ -283,6 +288,13 @@ __global__ void __launch_bounds__(32 * SpmvGroups<DIM>::P, 4) k_spmv(DevMesh m, 
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int e = blockIdx.x * 32 + lane;
   bool live = e < m.ne;
+  if (MODE == 0 && m.phase == 2) {
+    // fluid-only solve of the staggered scheme: displacement rows are identity
+    constexpr int R = SpmvGroups<DIM>::R, NED = Shape<DIM>::ned;
+    if (live)
+      for (int r = 0; r < R; ++r) y[(long long)e * NED + warp * R + r] = x[(long long)e * NED + warp * R + r];
+    return;
+  }
   if (live) {
     switch (warp) {
       case 0: spmv_group<T, DIM, MODE, 0>(m, dg, off, x, y, e); break;
@@ -500,7 +512,7 @@ __global__ void k_schur(DevMesh m, const T* __restrict__ lu, T* sinv) {
   constexpr int F = S::nfn, NED = S::ned, LUS = S::lus;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= m.np) return;
-  if (!m.p_active[g]) {
+  if (!m.p_active[g] || m.p_fixval[g] == m.p_fixval[g]) {
     sinv[g] = (T)1;
     return;
   }
@@ -732,8 +744,12 @@ __global__ void k_prec_p(DevMesh m, const T* __restrict__ rin, const double* sca
   T sc = scale ? (T)(*scale) : (T)1;
   T r = rin[m.nu + g] * sc;
   if (lane == 0 && vout) vout[m.nu + g] = r;
-  if (!m.p_active[g]) {
+  if (!m.p_active[g] || m.p_fixval[g] == m.p_fixval[g] || m.phase == 1) {
     if (lane == 0) z[m.nu + g] = r;
+    return;
+  }
+  if (m.phase == 2) {
+    if (lane == 0) z[m.nu + g] = (T)((double)r * m.sinv_d[g]);
     return;
   }
   const int t0 = m.pinc_ptr[g], nt = (m.pinc_ptr[g + 1] - t0) * F;
@@ -808,186 +824,584 @@ __device__ double block_sum_partials(const double* partial, int n, int stride, i
   return t;
 }
 
-// multi-dot: H[:, j] = V[:, 0..j]^T w, in chunks of 32 columns (w is
-// re-read per chunk, from L2)
+// ---------------------------------------------------------------- Gram-Schmidt
+// Classical Gram-Schmidt for Arnoldi step j in three kernels per pass, with
+// no serial tail in any of them:
+//   k_gs_dot  block partials of V[:, 0..j]^T w (and of ||w||^2);
+//   k_gs_sub  every CTA reduces the partial table itself (the same fixed
+//             order in every CTA, so all CTAs hold bit-identical
+//             coefficients), then w -= V h and block partials of ||w||^2;
+//   k_gs_fin  every CTA reduces the norm partials; block 0 applies the Givens
+//             rotations to column j (staged in shared memory), all CTAs write
+//             v_{j+1} = w / ||w||.  With selective re-orthogonalisation the
+//             same kernel instead starts the second pass (its dot products)
+//             when the first pass removed more than 1 - eta of ||w||.
+// The grid is one CTA per SM (GS_T threads), so a table row holds one
+// partial per SM.
+constexpr int GS_T = 512;
+constexpr int GS_MAXB = GS_MAXB_HOST;  // largest grid the partial tables hold
+
+// reduce-scatter of 32 per-lane values over the warp: afterwards lane l's
+// a[0] is the warp sum of a[l] (31 shuffles in a fixed butterfly order)
+template <int LEN, typename T> __device__ __forceinline__ void rs_stage(T* a, int lane) {
+  const bool up = (lane & LEN) != 0;
+#pragma unroll
+  for (int k = 0; k < LEN; ++k) {
+    const T send = up ? a[k] : a[k + LEN];
+    const T keep = up ? a[k + LEN] : a[k];
+    a[k] = keep + __shfl_xor_sync(0xffffffffu, send, LEN);
+  }
+}
+// 16 per-lane values summed over the warp: afterwards lane l < 16 holds the
+// warp sum of a[l] in a[0] (16 + 8 + 4 + 2 + 1 shuffles in a fixed order)
+template <typename T> __device__ __forceinline__ T warp_reduce_scatter16(T* a, int lane) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) a[k] += __shfl_xor_sync(0xffffffffu, a[k], 16);
+  rs_stage<8>(a, lane);
+  rs_stage<4>(a, lane);
+  rs_stage<2>(a, lane);
+  rs_stage<1>(a, lane);
+  return a[0];
+}
+
+// block partials of V[:, 0..j]^T w into part[blockIdx.x * GM_LD + c]; with
+// wnorm also of ||w||^2 into column GM_MAX.  Columns go in chunks of 16 (w is
+// re-read per chunk, from L2): 16 independent 16-byte loads per thread and
+// iteration already keep far more bytes in flight than HBM latency needs.
 template <typename T>
-__global__ void __launch_bounds__(RB) k_mdot(const T* __restrict__ V, long long ldv, int j, const T* __restrict__ w,
-                                             long long n, double* partial, int* counter, GmresState* gs, double* hout,
-                                             int with_wnorm, const int* skipflag) {
-  // with_wnorm: also ||w||^2 into gs->nrm2 (partial column GM_MAX is free:
-  // at most GM_MAX coefficient columns); skipflag: leave at once if set
-  if (gs->done || (skipflag && *skipflag)) return;
-  __shared__ double sm[RB / 32][32];
-  __shared__ bool last;
-  const int ncols = j + 1;
+__device__ void gs_partial_dots(const T* __restrict__ V, long long ldv, int ncols, const T* __restrict__ w,
+                                long long n, double* part, bool wnorm) {
   using VT = typename Vec<T>::type;
-  constexpr int VN = Vec<T>::n;
+  constexpr int VN = Vec<T>::n, NW = GS_T / 32, CH = 16;
+  __shared__ double ws[NW][CH + 1];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nv = n / VN;
-  constexpr int CH = sizeof(T) == 4 ? 32 : 16;   // columns per transpose pass (static smem < 48 KB)
-  __shared__ T tile[RB / 32][32][CH + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  double accw = 0.0;
-  for (int q0 = 0; q0 < ncols; q0 += 32) {
-    const int nq = min(32, ncols - q0);
+  for (int q0 = 0; q0 < ncols; q0 += CH) {
+    const int nq = min(CH, ncols - q0);
     const T* Vq = V + (long long)q0 * ldv;
-    const bool wn = with_wnorm && q0 == 0;
-    T acc[32];
+    const bool wn = wnorm && q0 == 0;
+    T acc[CH];
     T aw = (T)0;
 #pragma unroll
-    for (int c = 0; c < 32; ++c) acc[c] = (T)0;
+    for (int c = 0; c < CH; ++c) acc[c] = (T)0;
     for (long long iv = tid; iv < nv; iv += stride) {
-      VT wv = reinterpret_cast<const VT*>(w)[iv];
+      const VT wv = reinterpret_cast<const VT*>(w)[iv];
       if (wn) aw += Vec<T>::dot(wv, wv);
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
+      for (int c = 0; c < CH; ++c)
         if (c < nq) acc[c] += Vec<T>::dot(reinterpret_cast<const VT*>(Vq + c * ldv)[iv], wv);
     }
     for (long long i = nv * VN + tid; i < n; i += stride) {
-      T wv = w[i];
+      const T wv = w[i];
       if (wn) aw += wv * wv;
 #pragma unroll
-      for (int c = 0; c < 32; ++c)
+      for (int c = 0; c < CH; ++c)
         if (c < nq) acc[c] += Vq[c * ldv + i] * wv;
     }
-    accw += (double)aw;
-    // block reduction by transposition: warp w writes its 32 accumulators as
-    // row lane of a 32x32 tile; lane c then adds column c (working precision,
-    // 32 adds) and the warp results meet in double
-#pragma unroll
-    for (int c0 = 0; c0 < 32; c0 += CH) {
-#pragma unroll
-      for (int c = 0; c < CH; ++c) tile[warp][lane][c] = acc[c0 + c];
-      __syncwarp();
-      if (lane < CH) {
-        T colsum = (T)0;
-#pragma unroll
-        for (int l = 0; l < 32; ++l) colsum += tile[warp][l][lane];
-        sm[warp][c0 + lane] = (double)colsum;
-      }
-      __syncwarp();
+    const T col = warp_reduce_scatter16(acc, lane);
+    if (lane < CH) ws[warp][lane] = (double)col;
+    if (wn) {
+      const double s = warp_sum((double)aw);
+      if (lane == 0) ws[warp][CH] = s;
     }
     __syncthreads();
-    if (threadIdx.x < nq) {
+    if ((int)threadIdx.x < nq || (wn && threadIdx.x == CH)) {
+      const int c = threadIdx.x;
       double s = 0.0;
-      for (int wq = 0; wq < RB / 32; ++wq) s += sm[wq][threadIdx.x];
-      partial[(long long)blockIdx.x * GM_LD + q0 + threadIdx.x] = s;
+      for (int k = 0; k < NW; ++k) s += ws[k][c];
+      part[(long long)blockIdx.x * GM_LD + (c < CH ? q0 + c : GM_MAX)] = s;
     }
     __syncthreads();
-  }
-  if (with_wnorm) {
-    __shared__ double smw[RB / 32];
-    const double v = warp_sum(accw);
-    if (lane == 0) smw[warp] = v;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double s = 0.0;
-      for (int wq = 0; wq < RB / 32; ++wq) s += smw[wq];
-      partial[(long long)blockIdx.x * GM_LD + GM_MAX] = s;
-    }
-  }
-  __threadfence();
-  __syncthreads();
-  if (threadIdx.x == 0) last = (atomicAdd(counter, 1) == (int)gridDim.x - 1);
-  __syncthreads();
-  if (last) {
-    // per chunk of 32 columns: thread (grp, c) sums rows b = grp, grp+8, ...
-    // of the partial table, then column c adds the groups in order
-    __shared__ double red[RB / 32][32];
-    const int c = threadIdx.x & 31, grp = threadIdx.x >> 5;
-    for (int q0 = 0; q0 < ncols; q0 += 32) {
-      double sacc = 0.0;
-      if (q0 + c < ncols)
-        for (int b = grp; b < (int)gridDim.x; b += RB / 32) sacc += __ldcg(partial + (long long)b * GM_LD + q0 + c);
-      red[grp][c] = sacc;
-      __syncthreads();
-      if (threadIdx.x < 32 && q0 + (int)threadIdx.x < ncols) {
-        double tot = 0.0;
-        for (int g2 = 0; g2 < RB / 32; ++g2) tot += red[g2][threadIdx.x];
-        hout[q0 + threadIdx.x] = tot;
-      }
-      __syncthreads();
-    }
-    if (with_wnorm) {
-      // all threads of the last block share the sum (a serial loop over the
-      // blocks' partials would chain hundreds of L2 loads)
-      const double s = block_sum_partials(partial + GM_MAX, gridDim.x, GM_LD, 0);
-      if (threadIdx.x == 0) gs->nrm2 = s;
-    }
-    if (threadIdx.x == 0) *counter = 0;
   }
 }
 
-// w -= V h; ||w||; Givens update of column j; convergence test
-template <typename T>
-__global__ void __launch_bounds__(RB) k_orth(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
-                                             double* partial, int* counter, GmresState* gs, int mrest,
-                                             const double* hsrc, int mode, double eta, const int* skipflag) {
-  // w -= V hsrc, ||w||, then the Givens update of column j, by mode:
-  //   0: single pass;
-  //   1: second pass (hsrc = gs->h2, added to column j of H first);
-  //   2: first of two passes: if ||w|| kept at least eta of its length before
-  //      the pass (gs->nrm2), no second pass is needed: finish here and set
-  //      gs->skip2; otherwise leave column j to the second pass
-  if (gs->done || (skipflag && *skipflag)) return;
-  __shared__ T h[GM_MAX];
-  const int ncols = j + 1;
-  for (int c = threadIdx.x; c < GM_MAX; c += blockDim.x) h[c] = c < ncols ? (T)hsrc[c] : (T)0;
+// sums of the nb block partials of columns cols(v) = v < ncols ? v : GM_MAX
+// (v < nvc) into out[], by the whole CTA: thread (group, column) adds the rows
+// group, group + groups, ... (independent loads, several in flight), then the
+// groups meet in a fixed order
+__device__ void gs_reduce_table(const double* part, int nb, int ncols, int nvc, double* out) {
+  __shared__ double red[GS_T];
+  const int cw = nvc <= 32 ? 32 : nvc <= 64 ? 64 : 128;
+  const int groups = GS_T / cw;
+  const int c = threadIdx.x % cw, grp = threadIdx.x / cw;
+  double s = 0.0;
+  if (c < nvc) {
+    const int col = c < ncols ? c : GM_MAX;
+    int b = grp;
+    for (; b + 3 * groups < nb; b += 4 * groups) {
+      const double v0 = __ldcg(part + (long long)b * GM_LD + col);
+      const double v1 = __ldcg(part + (long long)(b + groups) * GM_LD + col);
+      const double v2 = __ldcg(part + (long long)(b + 2 * groups) * GM_LD + col);
+      const double v3 = __ldcg(part + (long long)(b + 3 * groups) * GM_LD + col);
+      s += v0;
+      s += v1;
+      s += v2;
+      s += v3;
+    }
+    for (; b < nb; b += groups) s += __ldcg(part + (long long)b * GM_LD + col);
+  }
+  red[threadIdx.x] = s;
   __syncthreads();
-  T acc_t = (T)0;
+  if ((int)threadIdx.x < nvc) {
+    double t = 0.0;
+    for (int g = 0; g < groups; ++g) t += red[g * cw + threadIdx.x];
+    out[threadIdx.x < (unsigned)ncols ? threadIdx.x : GM_MAX] = t;
+  }
+  __syncthreads();
+}
+
+// sum of nb doubles (one per block), the same fixed order in every CTA
+__device__ double gs_reduce_vector(const double* p, int nb) {
+  __shared__ double sw[GS_T / 32];
+  double v = 0.0;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) v += __ldcg(p + b);
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sw[warp] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int k = 0; k < GS_T / 32; ++k) t += sw[k];
+  __syncthreads();
+  return t;
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GS_T) k_gs_dot(const T* __restrict__ V, long long ldv, int j,
+                                                 const T* __restrict__ w, long long n, double* part,
+                                                 const GmresState* gs, int wnorm) {
+  if (gs->done) return;
+  gs_partial_dots<T>(V, ldv, j + 1, w, n, part, wnorm != 0);
+}
+
+// w -= V h with h the reduced first-pass (first = 1, stored into column j of
+// H, and ||w||^2 before the pass into gs->nrm2) or second-pass coefficients
+// (into gs->h2); block partials of the new ||w||^2 into part2
+template <typename T>
+__global__ void __launch_bounds__(GS_T) k_gs_sub(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
+                                                 const double* part, double* part2, GmresState* gs, int first,
+                                                 int wnorm, const int* skipflag) {
+  if (gs->done || (skipflag && *skipflag)) return;
+  __shared__ double hs[GM_LD];
+  __shared__ T ht[GM_MAX];
+  const int ncols = j + 1;
+  const int nb = gridDim.x;
+  gs_reduce_table(part, nb, ncols, ncols + (first && wnorm ? 1 : 0), hs);
+  for (int c = threadIdx.x; c < ncols; c += blockDim.x) ht[c] = (T)hs[c];
+  if (blockIdx.x == 0) {
+    double* dst = first ? gs->H + j * GM_LD : gs->h2;
+    for (int c = threadIdx.x; c < ncols; c += blockDim.x) dst[c] = hs[c];
+    if (first && wnorm && threadIdx.x == 0) gs->nrm2 = hs[GM_MAX];
+  }
+  __syncthreads();
   using VT = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n;
   const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nv = n / VN;
+  T acc = (T)0;
   for (long long iv = tid; iv < nv; iv += stride) {
     VT ww = reinterpret_cast<const VT*>(w)[iv];
 #pragma unroll 8
-    for (int c = 0; c < ncols; ++c) Vec<T>::axpy(ww, h[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
+    for (int c = 0; c < ncols; ++c) Vec<T>::axpy(ww, ht[c], reinterpret_cast<const VT*>(V + c * ldv)[iv]);
     reinterpret_cast<VT*>(w)[iv] = ww;
-    acc_t += Vec<T>::dot(ww, ww);
+    acc += Vec<T>::dot(ww, ww);
   }
   for (long long i = nv * VN + tid; i < n; i += stride) {
     T ww = w[i];
-    for (int c = 0; c < ncols; ++c) ww -= h[c] * V[c * ldv + i];
+    for (int c = 0; c < ncols; ++c) ww -= ht[c] * V[c * ldv + i];
     w[i] = ww;
-    acc_t += ww * ww;
+    acc += ww * ww;
   }
-  if (!block_partial_last((double)acc_t, partial, counter)) return;
-  double nrm2 = block_sum_partials(partial, gridDim.x, 1, 0);
+  __shared__ double sw[GS_T / 32];
+  const double v = warp_sum((double)acc);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  if (lane == 0) sw[warp] = v;
+  __syncthreads();
   if (threadIdx.x == 0) {
-    double nrm = sqrt(nrm2);
-    double* hc = gs->H + j * GM_LD;
-    if (mode == 2) {
-      const double before = sqrt(gs->nrm2);
-      const bool enough = nrm >= eta * before || !(before > 0.0);
-      gs->skip2 = enough ? 1 : 0;
-      if (!enough) {
-        *counter = 0;
-        return;
+    double t = 0.0;
+    for (int k = 0; k < GS_T / 32; ++k) t += sw[k];
+    part2[blockIdx.x] = t;
+  }
+}
+
+// the end of a Gram-Schmidt pass, by mode:
+//   0: single pass: finish (Givens on column j, v_{j+1} = w / ||w||);
+//   1: second pass: H[:, j] += h2, then finish;
+//   2: first of two passes: finish if ||w|| kept at least eta of its length
+//      (gs->nrm2 is ||w||^2 before the pass) and set gs->skip2; otherwise
+//      clear gs->skip2 and write the second pass's block partials of V^T w
+template <typename T>
+__global__ void __launch_bounds__(GS_T) k_gs_fin(const T* __restrict__ V_in, T* Vnext, long long ldv, int j,
+                                                 const T* __restrict__ w, long long n, const double* part2,
+                                                 double* part, GmresState* gs, int mrest, int mode, double eta,
+                                                 const int* skipflag) {
+  if (gs->done || (skipflag && *skipflag)) return;
+  const int nb = gridDim.x;
+  const double nrm2 = gs_reduce_vector(part2, nb);
+  const double nrm = sqrt(nrm2);
+  bool finish = true;
+  if (mode == 2) {
+    const double before = sqrt(gs->nrm2);
+    finish = nrm >= eta * before || !(before > 0.0);
+  }
+  if (!finish) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+      gs->skip2 = 0;
+      gs->reorths += 1;
+      gs->reorth_cols += j + 1;
+    }
+    gs_partial_dots<T>(V_in, ldv, j + 1, w, n, part, false);
+    return;
+  }
+  if (blockIdx.x == 0) {
+    __shared__ double hc[GM_LD], csd[GM_MAX], snd[GM_MAX];
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      hc[i] = gs->H[j * GM_LD + i] + (mode == 1 ? gs->h2[i] : 0.0);
+      if (i < j) {
+        csd[i] = gs->cs[i];
+        snd[i] = gs->sn[i];
       }
     }
-    if (mode == 1)
-      for (int i = 0; i <= j; ++i) hc[i] += hsrc[i];
-    for (int i = 0; i < j; ++i) {
-      double a = hc[i], b = hc[i + 1];
-      hc[i] = gs->cs[i] * a + gs->sn[i] * b;
-      hc[i + 1] = -gs->sn[i] * a + gs->cs[i] * b;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int i = 0; i < j; ++i) {
+        const double a = hc[i], b = hc[i + 1];
+        hc[i] = csd[i] * a + snd[i] * b;
+        hc[i + 1] = -snd[i] * a + csd[i] * b;
+      }
+      const double a = hc[j];
+      const double den = hypot(a, nrm);
+      const double cs = den > 0.0 ? a / den : 1.0, sn = den > 0.0 ? nrm / den : 0.0;
+      hc[j] = den;
+      hc[j + 1] = 0.0;
+      gs->cs[j] = cs;
+      gs->sn[j] = sn;
+      const double gj = gs->g[j];
+      gs->g[j + 1] = -sn * gj;
+      gs->g[j] = cs * gj;
+      gs->inv_h = nrm > 0.0 ? 1.0 / nrm : 0.0;
+      gs->iters += 1;
+      gs->jlast = j + 1;
+      if (mode == 2) gs->skip2 = 1;
+      if (fabs(gs->g[j + 1]) <= gs->tol_abs || j + 1 >= mrest || !(nrm > 0.0) || !isfinite(nrm)) gs->done = 1;
     }
-    double a = hc[j];
-    double den = hypot(a, nrm);
-    double cs = den > 0.0 ? a / den : 1.0, sn = den > 0.0 ? nrm / den : 0.0;
-    hc[j] = den;
-    hc[j + 1] = 0.0;
-    gs->cs[j] = cs;
-    gs->sn[j] = sn;
-    gs->g[j + 1] = -sn * gs->g[j];
-    gs->g[j] = cs * gs->g[j];
-    gs->inv_h = nrm > 0.0 ? 1.0 / nrm : 0.0;
-    gs->iters += 1;
-    gs->jlast = j + 1;
-    if (fabs(gs->g[j + 1]) <= gs->tol_abs || j + 1 >= mrest || !(nrm > 0.0) || !isfinite(nrm)) gs->done = 1;
-    *counter = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j + 1; i += blockDim.x) gs->H[j * GM_LD + i] = hc[i];
   }
+  // v_{j+1} = w / ||w||: every CTA took the same norm from the same partials
+  const T sc = (T)(nrm > 0.0 ? 1.0 / nrm : 0.0);
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  for (long long iv = tid; iv < nv; iv += stride)
+    reinterpret_cast<VT*>(Vnext)[iv] = Vec<T>::scale(reinterpret_cast<const VT*>(w)[iv], sc);
+  for (long long i = nv * VN + tid; i < n; i += stride) Vnext[i] = w[i] * sc;
+}
+
+// ------------------------------------------------------- delayed CGS2 Arnoldi
+// Gram-Schmidt with the re-orthogonalisation of each basis vector delayed by
+// one Arnoldi step and fused with the next step's projection (the
+// low-synchronisation "DCGS2" scheme of Bielich, Langou, Thomas,
+// Swirydowicz, Yamazaki and Boman): two sweeps over the basis and one
+// global reduction per step, with the orthogonality of two-pass classical
+// Gram-Schmidt.
+//
+// At step j >= 1 the basis holds Q = [v_0 .. v_{j-1}] (final, orthonormal)
+// and the lagged vector u_j (projected once, not normalised) in column j;
+// w = A M^-1 u_j has been formed.  One reduction gives
+//   a = Q^T u_j, b = Q^T w, alpha = u_j.u_j, beta = u_j.w,
+// then
+//   r = sqrt(alpha - a.a),  v_j = (u_j - Q a) / r              (re-orthogonalised)
+//   column j-1 of the Hessenberg matrix H: += a, subdiagonal r   (now final)
+//   c = H[0..j, 0..j-1] a  (the Arnoldi relation A M^-1 Q = V H)
+//   column j (tentative): h_i = (b_i - c_i) / r (i < j), h_j = ((beta - a.b)/r - c_j)/r
+//   u_{j+1} = (w - Q b - d v_j) / r with d = (beta - a.b) / r  (projected once)
+// so the sweep needs only a, b, r and d; H and its Givens rotations are kept
+// by block 0 alone, which does no sweep.  Step 0 has v_0 final: r = 1, no a.
+// The convergence test of column j-1 runs at step j; at the end of a cycle a
+// last reduction finalises column m-1.
+constexpr int DC_LD = 2 * GM_MAX + 2;  // row length of the reduction table
+constexpr int DC_SLAB = 4096;                           // doubles staged at a time by dc_reduce
+constexpr size_t DC_SMEM = DC_SLAB * sizeof(double);   // 32 KiB of dynamic shared memory
+
+// block partials of [Q^T u, Q^T w, u.u, u.w] (w != null) or [Q^T u, u.u]
+template <typename T>
+__global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long long ldv, int j,
+                                                 const T* __restrict__ w, long long n, double* part,
+                                                 const GmresState* gs) {
+  if (gs->done) return;
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n, NW = GS_T / 32, CH = sizeof(T) == 4 ? 16 : 8;
+  __shared__ double ws[NW][2 * CH + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  const T* u = V + (long long)j * ldv;
+  const bool hw = w != nullptr;
+  double* row = part + (long long)blockIdx.x * DC_LD;
+  const int nchunks = j > 0 ? (j + CH - 1) / CH : 1;
+  for (int ch = 0; ch < nchunks; ++ch) {
+    const int q0 = ch * CH, nq = max(0, min(CH, j - q0));
+    const T* Vq = V + (long long)q0 * ldv;
+    const bool first = ch == 0;
+    T au[CH], aw[CH];
+    T uu = (T)0, uw = (T)0;
+#pragma unroll
+    for (int c = 0; c < CH; ++c) au[c] = aw[c] = (T)0;
+    for (long long iv = tid; iv < nv; iv += stride) {
+      const VT uv = reinterpret_cast<const VT*>(u)[iv];
+      VT wv = Vec<T>::zero();
+      if (hw) wv = reinterpret_cast<const VT*>(w)[iv];
+      if (first) {
+        uu += Vec<T>::dot(uv, uv);
+        if (hw) uw += Vec<T>::dot(uv, wv);
+      }
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (c < nq) {
+          const VT q = reinterpret_cast<const VT*>(Vq + c * ldv)[iv];
+          au[c] += Vec<T>::dot(q, uv);
+          if (hw) aw[c] += Vec<T>::dot(q, wv);
+        }
+    }
+    for (long long i = nv * VN + tid; i < n; i += stride) {
+      const T uv = u[i], wv = hw ? w[i] : (T)0;
+      if (first) {
+        uu += uv * uv;
+        uw += uv * wv;
+      }
+#pragma unroll
+      for (int c = 0; c < CH; ++c)
+        if (c < nq) {
+          au[c] += Vq[c * ldv + i] * uv;
+          aw[c] += Vq[c * ldv + i] * wv;
+        }
+    }
+    // per warp: lanes c < CH hold column c of both sets
+    T su, sw;
+    if (CH == 16) {
+      su = warp_reduce_scatter16(au, lane);
+      sw = hw ? warp_reduce_scatter16(aw, lane) : (T)0;
+    } else {
+      // 8 columns over 32 lanes: full sums across lane bits 4 and 3, then
+      // the reduce-scatter over bits 2..0 leaves column l in lane l (< 8)
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        au[k] += __shfl_xor_sync(0xffffffffu, au[k], 16);
+        aw[k] += __shfl_xor_sync(0xffffffffu, aw[k], 16);
+      }
+#pragma unroll
+      for (int k = 0; k < CH; ++k) {
+        au[k] += __shfl_xor_sync(0xffffffffu, au[k], 8);
+        aw[k] += __shfl_xor_sync(0xffffffffu, aw[k], 8);
+      }
+      rs_stage<4>(au, lane); rs_stage<2>(au, lane); rs_stage<1>(au, lane);
+      rs_stage<4>(aw, lane); rs_stage<2>(aw, lane); rs_stage<1>(aw, lane);
+      su = au[0];
+      sw = aw[0];
+    }
+    if (lane < CH) {
+      ws[warp][lane] = (double)su;
+      ws[warp][CH + lane] = (double)sw;
+    }
+    if (first) {
+      const double a = warp_sum((double)uu), b = warp_sum((double)uw);
+      if (lane == 0) {
+        ws[warp][2 * CH] = a;
+        ws[warp][2 * CH + 1] = b;
+      }
+    }
+    __syncthreads();
+    const int t = threadIdx.x;
+    if (t < 2 * CH + 2) {
+      double s = 0.0;
+      for (int k = 0; k < NW; ++k) s += ws[k][t];
+      if (t < CH) {
+        if (t < nq) row[q0 + t] = s;
+      } else if (t < 2 * CH) {
+        if (hw && t - CH < nq) row[j + q0 + t - CH] = s;
+      } else if (first) {
+        if (t == 2 * CH) row[hw ? 2 * j : j] = s;
+        else if (hw) row[2 * j + 1] = s;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// column sums of the nb x nvc table (row length DC_LD) into out[0..nvc), by
+// the whole CTA: the table is staged through shared memory in slabs of rows
+// (coalesced, all loads in flight), then each column is added in row order,
+// the same order in every CTA
+__device__ void dc_reduce(const double* part, int nb, int nvc, double* out) {
+  extern __shared__ double stage[];
+  const int rows_per = max(1, DC_SLAB / max(nvc, 1));
+  for (int c = threadIdx.x; c < nvc; c += blockDim.x) out[c] = 0.0;
+  for (int r0 = 0; r0 < nb; r0 += rows_per) {
+    const int nr = min(rows_per, nb - r0);
+    __syncthreads();
+    for (int t = threadIdx.x; t < nr * nvc; t += blockDim.x) {
+      const int rr = t / nvc, c = t - rr * nvc;
+      stage[t] = __ldcg(part + (long long)(r0 + rr) * DC_LD + c);
+    }
+    __syncthreads();
+    for (int c = threadIdx.x; c < nvc; c += blockDim.x) {
+      double s = out[c];
+      for (int rr = 0; rr < nr; ++rr) s += stage[rr * nvc + c];
+      out[c] = s;
+    }
+  }
+  __syncthreads();
+}
+
+// Givens rotations of the final column jc (hc, jc + 2 entries, rotated in
+// place) and the convergence test on |g_{jc+1}|, by one block: the earlier
+// rotations are staged in shared memory, thread 0 applies them
+__device__ void dc_givens_block(GmresState* gs, double* hc, int jc, int mrest) {
+  __shared__ double csd[GM_MAX], snd[GM_MAX];
+  for (int i = threadIdx.x; i < jc; i += blockDim.x) {
+    csd[i] = gs->cs[i];
+    snd[i] = gs->sn[i];
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < jc; ++i) {
+      const double a = hc[i], b = hc[i + 1];
+      hc[i] = csd[i] * a + snd[i] * b;
+      hc[i + 1] = -snd[i] * a + csd[i] * b;
+    }
+    const double a = hc[jc], sub = hc[jc + 1];
+    const double den = hypot(a, sub);
+    const double cs = den > 0.0 ? a / den : 1.0, sn = den > 0.0 ? sub / den : 0.0;
+    hc[jc] = den;
+    hc[jc + 1] = 0.0;
+    gs->cs[jc] = cs;
+    gs->sn[jc] = sn;
+    const double gj = gs->g[jc];
+    gs->g[jc + 1] = -sn * gj;
+    gs->g[jc] = cs * gj;
+    gs->iters = jc + 1;
+    gs->jlast = jc + 1;
+    if (fabs(gs->g[jc + 1]) <= gs->tol_abs || jc + 1 >= mrest || !(sub > 0.0) || !isfinite(sub)) gs->done = 1;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i <= jc + 1; i += blockDim.x) gs->H[jc * GM_LD + i] = hc[i];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(GS_T) k_dc_upd(T* V, long long ldv, int j, const T* __restrict__ w, long long n,
+                                                 const double* part, GmresState* gs, int mrest) {
+  if (gs->done) return;
+  __shared__ double red[DC_LD];
+  __shared__ T coef[2 * GM_MAX];
+  __shared__ double hc[GM_LD + 1], cvec[GM_LD];
+  const int nb = gridDim.x;
+  const int nvc = 2 * j + 2;
+  dc_reduce(part, nb, nvc, red);
+  const double uu = red[2 * j], uw = red[2 * j + 1];
+  double ab = 0.0, aa = 0.0;
+  for (int k = 0; k < j; ++k) {
+    ab += red[k] * red[j + k];
+    aa += red[k] * red[k];
+  }
+  const double r2 = uu - aa;
+  const double r = j == 0 ? 1.0 : (r2 > 0.0 ? sqrt(r2) : 0.0);
+  const double inv_r = r > 0.0 ? 1.0 / r : 0.0;
+  const double d = (uw - ab) * inv_r;
+  if (blockIdx.x == 0) {
+    // Hessenberg bookkeeping (no sweep in this block)
+    if (j == 0) {
+      if (threadIdx.x == 0) gs->Hr[0] = uw;
+      return;
+    }
+    double* Hr = gs->Hr;
+    for (int i = threadIdx.x; i < j; i += blockDim.x) hc[i] = Hr[(j - 1) * GM_LD + i] + red[i];
+    if (threadIdx.x == 0) hc[j] = r;
+    __syncthreads();
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) Hr[(j - 1) * GM_LD + i] = hc[i];
+    // c = H[0..j, 0..j-1] a with column j-1 from hc: thread (row i, group g)
+    // adds columns g, g+4, ... (independent loads), the groups then meet in
+    // order
+    {
+      __shared__ double cpart[4][128];
+      const int i = threadIdx.x & 127, g = threadIdx.x >> 7;
+      double ci = 0.0;
+      if (i <= j) {
+#pragma unroll 4
+        for (int k = g; k < j - 1; k += 4)
+          if (i <= k + 1) ci += Hr[k * GM_LD + i] * red[k];
+      }
+      cpart[g][i] = ci;
+      __syncthreads();
+      if (threadIdx.x <= (unsigned)j)
+        cvec[threadIdx.x] = ((cpart[0][threadIdx.x] + cpart[1][threadIdx.x]) + (cpart[2][threadIdx.x] +
+                            cpart[3][threadIdx.x])) + hc[threadIdx.x] * red[j - 1];
+      __syncthreads();
+    }
+    if (r > 0.0)
+      for (int i = threadIdx.x; i <= j; i += blockDim.x)
+        Hr[j * GM_LD + i] = i < j ? (red[j + i] - cvec[i]) * inv_r : (d - cvec[j]) * inv_r;
+    dc_givens_block(gs, hc, j - 1, mrest);
+    return;
+  }
+  for (int k = threadIdx.x; k < j; k += blockDim.x) {
+    coef[k] = (T)red[k];
+    coef[GM_MAX + k] = (T)red[j + k];
+  }
+  __syncthreads();
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  const T ir = (T)inv_r, dd = (T)d;
+  const long long stride = (long long)(gridDim.x - 1) * blockDim.x;
+  const long long tid = (blockIdx.x - 1) * (long long)blockDim.x + threadIdx.x;
+  const long long nv = n / VN;
+  T* u = V + (long long)j * ldv;
+  T* un = V + (long long)(j + 1) * ldv;
+  for (long long iv = tid; iv < nv; iv += stride) {
+    VT uq = reinterpret_cast<const VT*>(u)[iv];
+    VT wq = reinterpret_cast<const VT*>(w)[iv];
+#pragma unroll 8
+    for (int k = 0; k < j; ++k) {
+      const VT q = reinterpret_cast<const VT*>(V + k * ldv)[iv];
+      Vec<T>::axpy(uq, coef[k], q);
+      Vec<T>::axpy(wq, coef[GM_MAX + k], q);
+    }
+    const VT vj = Vec<T>::scale(uq, ir);
+    Vec<T>::axpy(wq, dd, vj);
+    if (j > 0) reinterpret_cast<VT*>(u)[iv] = vj;
+    reinterpret_cast<VT*>(un)[iv] = Vec<T>::scale(wq, ir);
+  }
+  for (long long i = nv * VN + tid; i < n; i += stride) {
+    T uq = u[i], wq = w[i];
+    for (int k = 0; k < j; ++k) {
+      uq -= coef[k] * V[k * ldv + i];
+      wq -= coef[GM_MAX + k] * V[k * ldv + i];
+    }
+    const T vj = uq * ir;
+    if (j > 0) u[i] = vj;
+    un[i] = (wq - dd * vj) * ir;
+  }
+}
+
+// end of a cycle that ran all mrest steps: finalise column mrest - 1 from
+// the reduction of [Q^T u_m, u_m.u_m]
+__global__ void __launch_bounds__(GS_T) k_dc_close(const double* part, int nb, int m, GmresState* gs) {
+  if (gs->done) return;
+  __shared__ double red[DC_LD];
+  __shared__ double hc[GM_LD + 1];
+  dc_reduce(part, nb, m + 1, red);
+  double aa = 0.0;
+  for (int k = 0; k < m; ++k) aa += red[k] * red[k];
+  const double r2 = red[m] - aa;
+  const double r = r2 > 0.0 ? sqrt(r2) : 0.0;
+  for (int i = threadIdx.x; i < m; i += blockDim.x) hc[i] = gs->Hr[(m - 1) * GM_LD + i] + red[i];
+  if (threadIdx.x == 0) hc[m] = r;
+  __syncthreads();
+  for (int i = threadIdx.x; i <= m; i += blockDim.x) gs->Hr[(m - 1) * GM_LD + i] = hc[i];
+  __syncthreads();
+  dc_givens_block(gs, hc, m - 1, m);
+  if (threadIdx.x == 0) gs->done = 1;
 }
 
 template <typename T>
@@ -1003,14 +1417,23 @@ __global__ void k_scale_into(const T* __restrict__ w, T* v, long long n, const d
   for (long long i = nv * VN + tid; i < n; i += stride) v[i] = w[i] * sc;
 }
 
-__global__ void k_backsolve(GmresState* gs) {
-  if (threadIdx.x != 0) return;
-  int jl = gs->jlast;
+// y = R^-1 g for the rotated Hessenberg matrix of the cycle: the jl x jl
+// triangle is staged in shared memory by the whole block, then solved column
+// by column (each step one division and a parallel update)
+__global__ void __launch_bounds__(256) k_backsolve(GmresState* gs, int mrest) {
+  extern __shared__ double Hs[];  // mrest columns of GM_LD, then the right-hand side
+  const int jl = gs->jlast;
+  double* rhs = Hs + (size_t)mrest * GM_LD;
+  for (int t = threadIdx.x; t < jl * GM_LD; t += blockDim.x) Hs[t] = gs->H[t];
+  for (int t = threadIdx.x; t < jl; t += blockDim.x) rhs[t] = gs->g[t];
+  __syncthreads();
   for (int i = jl - 1; i >= 0; --i) {
-    double s = gs->g[i];
-    for (int k = i + 1; k < jl; ++k) s -= gs->H[k * GM_LD + i] * gs->y[k];
-    double d = gs->H[i * GM_LD + i];
-    gs->y[i] = d != 0.0 ? s / d : 0.0;
+    const double d = Hs[i * GM_LD + i];
+    const double yi = d != 0.0 ? rhs[i] / d : 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) gs->y[i] = yi;
+    for (int k = threadIdx.x; k < i; k += blockDim.x) rhs[k] -= Hs[i * GM_LD + k] * yi;
+    __syncthreads();
   }
 }
 
@@ -1157,6 +1580,42 @@ __global__ void __launch_bounds__(RB) k_newton_update(DevMesh m, double* X, cons
   }
 }
 
+// fluid-only solves: inverse diagonal of the (scaled) pressure block D
+template <int DIM>
+__global__ void k_diag_d(DevMesh m) {
+  using S = Shape<DIM>;
+  using L = NL<DIM>;
+  constexpr int F = S::nfn;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= m.np) return;
+  double dsum = 0.0;
+  if (m.p_active[g] && !(m.p_fixval[g] == m.p_fixval[g]))
+    for (int t = m.pinc_ptr[g]; t < m.pinc_ptr[g + 1]; ++t) {
+      const int f = m.pinc_face[t];
+      if (!m.beta[f]) continue;
+      const int ga = m.pinc_a[t];
+      dsum += m.nl[(long long)f * S::nld + L::Dm + ga * F + ga];
+    }
+  const double d = m.scal[0] * dsum;
+  m.sinv_d[g] = fabs(d) > 1e-300 ? 1.0 / d : 1.0;
+}
+
+// b = -R on the rows of one block, zero on the other (staggered scheme):
+// keep_u / keep_p select the displacement and pressure rows
+__global__ void k_neg_part(const double* __restrict__ R, double* b, long long nu, long long n, int keep_u,
+                           int keep_p) {
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride)
+    b[i] = ((i < nu) ? keep_u : keep_p) ? -R[i] : 0.0;
+}
+
+template <typename T>
+__global__ void k_copy(const T* __restrict__ a, T* b, long long n, const int* skip) {
+  if (skip && *skip) return;
+  long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = a[i];
+}
+
 // ------------------------------------------------------------------ host side
 hf_status set_error(hf_mesh* h, hf_status s, const std::string& msg) {
   h->err = msg;
@@ -1292,11 +1751,18 @@ hf_status solver_alloc(hf_mesh* h) {
   size_t nmat = (size_t)h->ne * (h->ned * h->ned + (h->dim + 1) * h->ned * h->nfr);
   h->J32.dg = dalloc<float>(h, nmat);
   h->J32.off = h->J32.dg + (size_t)h->ne * h->ned * h->ned;
-  h->d_partial = dalloc<double>(h, (size_t)h->red_blocks * GM_LD);
+  h->d_partial = dalloc<double>(h, std::max((size_t)h->red_blocks * GM_LD, (size_t)GS_MAXB * DC_LD));
+  h->d_part2 = dalloc<double>(h, GS_MAXB);
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    h->gs_blocks = std::max(1, std::min(GS_MAXB, sms));
+  }
   h->d_gs = dalloc<GmresState>(h, 1);
   if (!h->K64.V || !h->K64.w || !h->K64.z || !h->K64.u || !h->K64.x || !h->K64.b || !h->K32.V ||
       !h->K32.w || !h->K32.z || !h->K32.u || !h->K32.x || !h->K32.b || !h->K64.lu || !h->K32.lu ||
-      !h->K64.sinv || !h->K32.sinv || !h->J32.dg || !h->d_partial || !h->d_gs)
+      !h->K64.sinv || !h->K32.sinv || !h->J32.dg || !h->d_partial || !h->d_part2 || !h->d_gs)
     return set_error(h, HF_ERR_OOM, "device allocation of the solver workspace failed");
   cudaMemsetAsync(h->K64.lu, 0, lus * sizeof(double), h->stream);
   cudaMemsetAsync(h->K32.lu, 0, lus * sizeof(float), h->stream);
@@ -1382,17 +1848,38 @@ static void precond(hf_mesh* h, const Krylov<T>& K, const T* rin, const double* 
   (void)vout;
   // warps (subdomains) per CTA: as many as keep at least two CTAs per SM busy
   int nsd = h->d.nsd;
+  if (h->d.phase == 2) {
+    // fluid-only solve: identity on the displacement rows, diagonal of D on
+    // the pressure rows
+    { note_launch(); k_copy<T><<<h->red_blocks, RB, 0, h->stream>>>(rin, z, h->nu, skip); }
+    if (h->np > 0)
+      { note_launch(); k_prec_p<T, DIM><<<(int)((h->np + 7) / 8), 256, 0, h->stream>>>(h->d, rin, nullptr, nullptr, K.sinv, z, skip); }
+    return;
+  }
   const bool coarse = h->opts.coarse && h->nc > 0;
+  // the coarse restriction and solve do not depend on the ILU(0) apply, which
+  // keeps only a few warps per SM busy: they run on the side stream beside it
+  // (joined before the prolongation).  Event-timed profiling keeps them on
+  // the handle's stream so every class is timed alone.
+  const bool fork = coarse && h->side && !(h->prof.on && !h->prof.capturing);
   if (coarse) {
-    prof_begin(h, PK_PREC_AUX);
-    coarse_pre<T, DIM>(h, K, rin, skip);
-    prof_end(h);
+    if (fork) {
+      cudaEventRecord(h->ev_fork, h->stream);
+      cudaStreamWaitEvent(h->side, h->ev_fork, 0);
+      coarse_pre<T, DIM>(h, K, rin, skip, h->side);
+      cudaEventRecord(h->ev_join, h->side);
+    } else {
+      prof_begin(h, PK_PREC_AUX);
+      coarse_pre<T, DIM>(h, K, rin, skip, h->stream);
+      prof_end(h);
+    }
   }
   prof_begin(h, PK_PREC);
   if (nsd >= 4 * 2 * 152) launch_apply<T, DIM, 4>(h, K.lu, rin, z, skip);
   else if (nsd >= 2 * 2 * 152) launch_apply<T, DIM, 2>(h, K.lu, rin, z, skip);
   else launch_apply<T, DIM, 1>(h, K.lu, rin, z, skip);
   prof_end(h);
+  if (fork) cudaStreamWaitEvent(h->stream, h->ev_join, 0);
   if (coarse || h->np > 0) {
     prof_begin(h, PK_PREC_AUX);
     if (coarse) coarse_post<T, DIM>(h, K, z, skip);
@@ -1409,29 +1896,56 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
   const int* done = &gs->done;
   long long N = h->N;
   int rb = 2 * 152;
-  int* cnt = h->d_count + 4;
+  const int nb = h->gs_blocks;
   for (int j = 0; j < mrest; ++j) {
     T* vj = K.V + (long long)j * K.ldv;
+    T* vnext = K.V + (long long)(j + 1) * K.ldv;
     h->prof.cap_j = j;
     precond<T, DIM>(h, K, vj, nullptr, nullptr, K.z, done);
     prof_begin(h, PK_SPMV);
     spmv<T, DIM, 0>(h, dg, off, K.z, K.w, done);
     prof_end(h);
     prof_begin(h, PK_ORTH);
-    const bool two = h->opts.reorth > 0;
+    if (h->opts.reorth == 3) {
+      { note_launch(); k_dc_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs); }
+      { note_launch(); k_dc_upd<T><<<nb, GS_T, DC_SMEM, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, mrest); }
+      prof_end(h);
+      continue;
+    }
     // reorth 1: a second pass only when the first removed more than 30% of
     // ||w|| (the Daniel-Gragg-Kaufman-Stewart test); reorth 2: always
+    const bool two = h->opts.reorth > 0;
     const double eta = h->opts.reorth == 2 ? HUGE_VAL : 0.7;
-    { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->H + j * GM_LD, two ? 1 : 0, nullptr); }
-    { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->H + j * GM_LD, two ? 2 : 0, eta, nullptr); }
+    { note_launch(); k_gs_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, two ? 1 : 0); }
+    { note_launch(); k_gs_sub<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, h->d_part2, gs, 1, two ? 1 : 0, nullptr); }
+    { note_launch(); k_gs_fin<T><<<nb, GS_T, 0, h->stream>>>(K.V, vnext, K.ldv, j, K.w, N, h->d_part2, h->d_partial, gs, mrest, two ? 2 : 0, eta, nullptr); }
     if (two) {
-      { note_launch(); k_mdot<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, gs->h2, 0, &gs->skip2); }
-      { note_launch(); k_orth<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, cnt, gs, mrest, gs->h2, 1, eta, &gs->skip2); }
+      { note_launch(); k_gs_sub<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, h->d_part2, gs, 0, 0, &gs->skip2); }
+      { note_launch(); k_gs_fin<T><<<nb, GS_T, 0, h->stream>>>(K.V, vnext, K.ldv, j, K.w, N, h->d_part2, h->d_partial, gs, mrest, 1, eta, &gs->skip2); }
     }
-    { note_launch(); k_scale_into<T><<<rb, RB, 0, h->stream>>>(K.w, K.V + (long long)(j + 1) * K.ldv, N, &gs->inv_h, done); }
     prof_end(h);
   }
-  { note_launch(); k_backsolve<<<1, 32, 0, h->stream>>>(gs); }
+  if (h->opts.reorth == 3) {
+    // a cycle that ran all mrest steps still has its last column to finalise
+    const T* um = K.V + (long long)mrest * K.ldv;
+    (void)um;
+    { note_launch(); k_dc_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, mrest, nullptr, N, h->d_partial, gs); }
+    { note_launch(); k_dc_close<<<1, GS_T, DC_SMEM, h->stream>>>(h->d_partial, nb, mrest, gs); }
+  }
+  {
+    const size_t sm = ((size_t)mrest * GM_LD + GM_LD) * sizeof(double);
+    static std::atomic<size_t> configured{0};
+    static std::mutex raise;
+    if (sm > 48 * 1024 && sm > configured.load()) {
+      std::lock_guard<std::mutex> lock(raise);
+      if (sm > configured.load()) {
+        cudaFuncSetAttribute(k_backsolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        configured.store(sm);
+      }
+    }
+    note_launch();
+    k_backsolve<<<1, 256, sm, h->stream>>>(gs, mrest);
+  }
   { note_launch(); k_combine<T><<<rb, RB, 0, h->stream>>>(K.V, K.ldv, N, gs, K.u); }
   precond<T, DIM>(h, K, K.u, nullptr, nullptr, K.z, nullptr);
   { note_launch(); k_axpy<T><<<rb, RB, 0, h->stream>>>(K.x, K.z, N); }
@@ -1441,7 +1955,7 @@ template <typename T, int DIM>
 static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest, cudaGraphExec_t* gexec,
                            std::vector<GraphEv>* gev) {
   long long& gk = sizeof(T) == 8 ? h->graph_kernels64 : h->graph_kernels32;
-  if (!h->opts.use_graphs) {
+  if (!h->opts.use_graphs || h->d.phase != 0) {
     gmres_cycle<T, DIM>(h, K, dg, off, mrest);
     return HF_OK;
   }
@@ -1489,6 +2003,9 @@ static hf_status read_gs(hf_mesh* h, CycleInfo* ci) {
   ci->beta = tmp.beta;
   ci->iters = tmp.iters;
   ci->done = tmp.done;
+  h->gs_reorths = tmp.reorths;
+  h->gs_reorth_cols = tmp.reorth_cols;
+  h->gs_cols += (long long)tmp.iters * (tmp.iters + 1) / 2;
   return HF_OK;
 }
 
@@ -1523,7 +2040,7 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
   // FP32 refinement sweeps first in mixed precision; when two sweeps in a
   // row fail to halve the FP64 residual (an FP32 operator too coarse for this
   // system), the solve goes on in FP64 from the current iterate
-  bool use64 = o.precision == HF_PREC_FP64, fell_back = false;
+  bool use64 = o.precision == HF_PREC_FP64 || h->d.phase != 0, fell_back = false;
   if (!use64) {
     Krylov<float>& K = h->K32;
     if (!h->j32_valid) convert_j32(h);
@@ -1552,7 +2069,12 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
       prev = rnorm;
       { note_launch(); k_demote_scaled<<<rb, RB, 0, h->stream>>>(r, K.b, N, h->d_red); }
       { note_launch(); k_fill<float><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0f); }
-      { note_launch(); k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs, o.inner_rtol); }
+      // each sweep reduces the residual by inner_rtol, except that a sweep
+      // needing less to reach the tolerance asks only for that (with a
+      // factor 0.3 of margin for the FP32 operator), so the last sweep does
+      // not overshoot the tolerance by orders of magnitude
+      const double inner = std::max(o.inner_rtol, std::min(0.5, 0.3 * tol / rnorm));
+      { note_launch(); k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs, inner); }
       { note_launch(); k_scale_into<float><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
       cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
       if ((st = run_cycle<float, DIM>(h, K, h->J32.dg, h->J32.off, mrest, &h->graph32, &h->gev32))) break;
@@ -1653,6 +2175,17 @@ hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]) {
   hf_status s = check_cuda(h, cudaStreamSynchronize(h->stream), "newton update");
   prof_flush(h);
   return s;
+}
+
+void launch_neg_part(hf_mesh* h, const double* R, double* b, int keep_u, int keep_p) {
+  { note_launch(); k_neg_part<<<h->red_blocks, RB, 0, h->stream>>>(R, b, h->nu, h->N, keep_u, keep_p); }
+}
+
+void launch_diag_d(hf_mesh* h) {
+  if (h->np <= 0) return;
+  note_launch();
+  if (h->dim == 2) k_diag_d<2><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d);
+  else k_diag_d<3><<<(int)((h->np + 127) / 128), 128, 0, h->stream>>>(h->d);
 }
 
 void launch_neg(hf_mesh* h, const double* a, double* b) {

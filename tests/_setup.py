@@ -51,7 +51,7 @@ def rel_err(a, b):
     return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
 
 
-def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
+def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=None):
     """One time step of Sec. 3 on the oracle, with the driver rules of
     hf_advance_step: Newton until converged, the criterion, Newton again if it
     switched facets (at most rounds_max rounds), end of step; an attempt that
@@ -60,7 +60,9 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
     each accepted sub-step until t + dt is reached; at most max_cutbacks
     failures in a row, 256 attempts in all.  Past newton_max an attempt goes
     on while the increments at least halve every iteration (at most
-    4 newton_max iterations)."""
+    4 newton_max iterations).  ``newton()`` replaces ``o.newton_step()``
+    (the same iteration with pooled assembly, say)."""
+    newton = newton or o.newton_step
     dt0 = o.prm.dt
     target = o.t + dt0
     sub = dt0
@@ -76,7 +78,7 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10):
         o.prm.dt = sub
         ok, rounds, it, prev = False, 0, 0, np.inf
         while True:
-            r = o.newton_step()
+            r = newton()
             rep["newton_iters"] += 1
             it += 1
             if not (np.isfinite(r["du_rel"]) and np.isfinite(r["dp_rel"])):

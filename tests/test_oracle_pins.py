@@ -589,3 +589,82 @@ def test_pressure_cutoff_converges_with_clipped_pressures():
     assert Pa.min() >= 0.0 and np.sum(Pa == 0.0) >= 1
     rep_off, Pa_off, _ = runs[False]
     assert not rep_off["converged"] and Pa_off.min() < -1e8
+
+
+# ------------------------------------------------------------------ staggered scheme (Sec. 4.3)
+def _given_length_kgd(n=12, L=24.0, ell=6.0):
+    """The given-length KGD crack of Sec. 4.1 / 4.3 in the viscosity regime
+    (E = 17 GPa, nu = 0.2, mu = 0.1 Pa s, Q0 = 1e-3 m^2/s, G_c = 120 Pa m,
+    dt = 1 s) on a square of side L, crack of half-length ell along the
+    midline, injection at the centre; for the staggered scheme zero pressure
+    at the pressure nodes nearest +-0.8 ell (a point behind each tip)."""
+    from hf_inputs import kgd_2d
+    E, nu, mu, Q0 = 17e9, 0.2, 0.1, 1e-3
+    Kic = kgd.kic_from_gc(120.0, E, nu)
+    wl = kgd_2d(n=n, length=L, E=E, nu=nu, K_Ic=Kic, sigma_c=1e6, mu=mu, Q0=Q0, dt=1.0, seed_cells=ell / (L / n))
+    pn = pressure_nodes(wl.mesh)
+    x, y = wl.mesh.xyz[pn, 0], wl.mesh.xyz[pn, 1]
+    on = np.abs(y) < 1e-9
+    fixed = sorted({int(np.argmin(np.abs(x - s * 0.8 * ell) + 1e9 * ~on)) for s in (1.0, -1.0)})
+    return wl, fixed
+
+
+def _given_length_oracle(wl, fixed=()):
+    inj, wts = wl.injection()
+    prm = Params(E=wl.E, nu=wl.nu, sigma_c=wl.sigma_c, delta_c=wl.delta_c, b_stab=10.0, mu=wl.mu, Q0=wl.Q0,
+                 inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=wl.delta_f, dt=1.0, L_ref=wl.fluid_length,
+                 cutoff_on=False, newton_tol=1e-10, fixed_pdofs=tuple(fixed), fixed_pvals=(0.0,) * len(fixed))
+    o = Oracle(wl.mesh, prm)
+    o.set_state(*wl.seed())
+    return o
+
+
+def test_staggered_scheme_fails_where_fully_coupled_converges():
+    """Sec. 4.3: with the injection rate imposed, the fully-coupled Newton
+    iteration converges quadratically from the seed guess, while the
+    staggered scheme (mechanics at the old pressure, then lubrication at the
+    new opening, with a fictitious zero pressure behind each tip) grows its
+    pressure increments and breaks down: the opening closes and the
+    decoupled fluid problem loses its conductivity."""
+    wl, fixed = _given_length_kgd()
+    o = _given_length_oracle(wl)
+    incs = []
+    for it in range(10):
+        r = o.newton_step()
+        incs.append(max(r["du_rel"], r["dp_rel"]))
+        if r["converged"]:
+            break
+    assert r["converged"] and it <= 6
+    assert incs[-1] < 1e-10 and incs[3] < 1e-2 * incs[2]   # quadratic once close
+    s = _given_length_oracle(wl, fixed)
+    dps = []
+    for it in range(10):
+        r = s.staggered_step()
+        dps.append(r["dp_rel"])
+        if not np.isfinite(r["dp_rel"]) or r["converged"]:
+            break
+    assert not r["converged"]
+    assert dps[1] > dps[0]                        # the pressure increments grow
+    assert not np.isfinite(dps[-1]) or min(dps) > 0.1
+
+
+def test_staggered_step_is_the_decoupled_block_solve():
+    """One staggered iteration solves exactly the decoupled block equations of
+    Eq. fully-coupled-fully-discrete: A dU = -R_u(U, P), then D dP =
+    -R_p(U + dU, P) at the updated opening (residuals of both at rounding
+    level against an independent assembly), and it leaves the fixed pressures
+    at their values."""
+    wl, fixed = _given_length_kgd(n=8, L=16.0, ell=4.0)
+    o = _given_length_oracle(wl, fixed)
+    U0, P0 = o.U.copy(), o.P.copy()
+    R, J = o.assemble()
+    Nu = o.Nu
+    o.staggered_step()
+    dU, dP = o.U - U0, o.P - P0
+    ru = J[:Nu, :Nu] @ dU + R[:Nu]
+    assert np.abs(ru).max() <= 1e-10 * np.abs(R[:Nu]).max()
+    R2, J2 = o.assemble(U=U0 + dU, P=P0)
+    rp = J2[Nu:, Nu:] @ dP + R2[Nu:]
+    assert np.abs(rp).max() <= 1e-10 * np.abs(R2[Nu:]).max()
+    assert np.abs(dP).max() > 0.0
+    assert np.all(o.P[fixed] == 0.0)

@@ -46,3 +46,35 @@ def test_noalloc_norms_match_newton_step_on_two_calls():
     st = lib.hf_increment_norms_noalloc(dx.data_ptr(), x1.data_ptr(), 1 << 26, 1, out.data_ptr(), None, err, 256)
     assert st == -1 and b"exceed" in err.value
     g.close()
+
+
+def test_noalloc_norms_multi_block_and_empty():
+    """Vectors spanning 3.5 scratch blocks of 16,384 unknowns with the
+    displacement/pressure split inside the third block: the last-block sum
+    over the block partials matches torch's sums, on two calls in a row (the
+    ticket is cleared per call); an empty call writes zeros."""
+    torch = pytest.importorskip("torch")
+    import paper_1911_10275_gb300 as pkg
+    lib = pkg.load()
+    chunk = 16384
+    n_u = 2 * chunk + 5000
+    n = int(3.5 * chunk)
+    n_p = n - n_u
+    gen = torch.Generator(device="cuda").manual_seed(11)
+    err = ctypes.create_string_buffer(256)
+    stream = torch.cuda.current_stream().cuda_stream
+    for call in range(2):
+        dx = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen)
+        x = torch.randn(n, dtype=torch.float64, device="cuda", generator=gen) * 3.0
+        out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+        st = lib.hf_increment_norms_noalloc(dx.data_ptr(), x.data_ptr(), n_u, n_p, out.data_ptr(), stream, err, 256)
+        assert st == 0, err.value
+        torch.cuda.synchronize()
+        want = torch.stack([(dx[:n_u] ** 2).sum(), (x[:n_u] ** 2).sum(), (dx[n_u:] ** 2).sum(),
+                            (x[n_u:] ** 2).sum()]).cpu().numpy()
+        assert np.allclose(out.cpu().numpy(), want, rtol=1e-12, atol=0)
+    out = torch.full((4,), -1.0, dtype=torch.float64, device="cuda")
+    st = lib.hf_increment_norms_noalloc(dx.data_ptr(), x.data_ptr(), 0, 0, out.data_ptr(), stream, err, 256)
+    assert st == 0, err.value
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), np.zeros(4))
