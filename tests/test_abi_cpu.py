@@ -36,7 +36,7 @@ def test_default_options_and_no_device_needed_for_defaults():
     lib = pkg.load()
     o = pkg.hf_solver_opts()
     lib.hf_default_solver_opts(ctypes.byref(o))
-    assert o.restart == 60 and o.reorth == 1 and o.coarse == 1 and o.precision == pkg.HF_PREC_FP64 and o.jacobi_block >= 1
+    assert o.restart == 60 and o.reorth == 3 and o.scheme == 0 and o.coarse == 1 and o.precision == pkg.HF_PREC_FP64 and o.jacobi_block >= 1
     assert lib.hf_last_error(None) == b"null handle"
 
 
