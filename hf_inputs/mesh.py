@@ -343,3 +343,31 @@ def batch_instances(count: int, seed: int = 191110275, ne_range=(1000, 50000)):
         out.append(dict(n=round_even(math.sqrt(ne[i] / 2.0)), E=float(E[i]), K_Ic=float(K[i]),
                         mu=float(mu[i]), Q0=float(Q0[i])))
     return out
+
+
+def far_field_load(mesh: Mesh, sigma0: float):
+    """A far-field stress sigma0 normal to the crack plane (compressive for
+    sigma0 > 0), as the outer load of the propagation test of the paper:
+    the rollers normal to the crack plane are removed from the face at
+    +L/2 along the crack normal, and that face carries the traction
+    -sigma0 n (n its outward normal); the opposite face keeps its rollers.
+    Returns (mesh with the reduced Dirichlet list, Neumann facets, their
+    tractions (n_neumann, dim))."""
+    ax, half, d = mesh.crack_normal_axis, mesh.length / 2, mesh.dim
+    edges = TRI_EDGES if d == 2 else TET_EDGES
+    n_en = mesh.n_en
+    top, drop = [], set()
+    for f in np.nonzero(mesh.face_elems[:, 1] < 0)[0]:
+        e = int(mesh.face_elems[f, 0])
+        fv = _local_face_vertices(d, int(mesh.face_local[f, 0]))
+        vx = mesh.xyz[mesh.elem_nodes[e, list(fv)]]
+        if np.all(np.abs(vx[:, ax] - half) < 1e-9 * half):
+            top.append(int(f))
+            loc = list(fv) + [d + 1 + k for k, (a, b) in enumerate(edges) if a in fv and b in fv]
+            for a in loc:
+                drop.add(e * n_en * d + a * d + ax)
+    keep = np.array([k not in drop for k in mesh.dir_dof.tolist()], dtype=bool)
+    m2 = dataclasses.replace(mesh, dir_dof=mesh.dir_dof[keep], dir_val=mesh.dir_val[keep])
+    trac = np.zeros((len(top), d))
+    trac[:, ax] = -sigma0
+    return m2, np.asarray(top, dtype=np.int32), trac

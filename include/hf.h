@@ -215,16 +215,19 @@ hf_status hf_apply_preconditioner(hf_mesh* h, const double* x, double* z);
 /* Solve J d = rhs with the configured GMRES (no state change); host vectors. */
 hf_status hf_solve_linear(hf_mesh* h, const double* rhs, double* d, hf_newton_report* rep);
 
-/* Profiling: with on != 0, every kernel class of the Newton step is bracketed
- * by CUDA events on the handle's stream (GMRES cycles are then launched
- * without graphs).  hf_get_kernel_times returns the accumulated milliseconds
- * and launch counts since profiling was switched on, per class:
- * 0 SpMV (Krylov precision), 1 preconditioner apply, 2 Gram-Schmidt + norm,
- * 3 ILU factorisation (and the coarse matrix), 4 assembly (facet terms +
- * residual), 5 FP64 SpMV of the refinement residual, 6 Newton update,
- * 7 the rest of the preconditioner (coarse restriction, solve and
- * prolongation; pressure rows).  Class 1 is the ILU(0) apply alone.  ms and
- * launches hold 8. */
+/* Profiling.  on = 1: every kernel class of the Newton step is bracketed by
+ * CUDA events on the handle's stream (GMRES cycles are then launched without
+ * graphs, the coarse level on the handle's stream).  on = 2: only each whole
+ * GMRES cycle is bracketed (graph replay or eager launches, as configured),
+ * nothing inside it.  on = 0: off.  hf_get_kernel_times returns the
+ * accumulated milliseconds and counts since profiling was switched on, per
+ * class: 0 SpMV (Krylov precision), 1 preconditioner apply, 2 Gram-Schmidt +
+ * norm, 3 ILU factorisation (and the coarse matrix), 4 assembly (facet terms
+ * + residual), 5 FP64 SpMV of the refinement residual, 6 Newton update, 7 the
+ * rest of the preconditioner (coarse restriction, solve and prolongation;
+ * pressure rows), each with its launch count; 8 whole GMRES cycles (mode 2)
+ * with the Arnoldi steps they finalised.  Class 1 is the ILU(0) apply
+ * alone.  ms and launches hold 9. */
 hf_status hf_set_profiling(hf_mesh* h, int on);
 hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
 /* Structure counts: [0] elements, [1] interior facet slots (element-side pairs
@@ -241,6 +244,18 @@ hf_status hf_get_kernel_times(hf_mesh* h, double* ms, int64_t* launches);
 hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
 
 const char* hf_last_error(const hf_mesh* h);
+
+/* Failure detection without a fault.  The preconditioner waits on mbarriers
+ * for its bulk copies with a bounded number of polls (default 2^22); a wait
+ * that runs out raises a device flag, the kernel goes on, and the solve
+ * returns HF_ERR_TIMEOUT with the context intact.  hf_set_wait_limit sets
+ * that bound (1..2^30 polls).  hf_check_wait_timeout runs the same bounded
+ * wait on a barrier that nothing ever completes (no copies issued) and
+ * returns HF_ERR_TIMEOUT once it has given up (HF_OK would mean the wait
+ * never gave up); the flag is cleared again, so the handle stays usable.
+ * The paper has no counterpart: this is the library's own robustness. */
+hf_status hf_set_wait_limit(hf_mesh* h, int64_t polls);
+hf_status hf_check_wait_timeout(hf_mesh* h);
 
 /* Allocation-free Newton convergence norms.  The paper has no counterpart:
  * this exists for callers that cannot allocate device memory (a process whose
@@ -298,7 +313,9 @@ void hf_default_step_opts(hf_step_opts* o);
  * tolerance, then the fracture criterion; if it switched facets, Newton
  * again (at most criterion_rounds rounds); then the end of the step
  * (hf_accept_step).  An attempt that does not converge within newton_max
- * iterations, whose linear solve does not converge, or whose state turns
+ * iterations, whose linear solve misses its tolerance by more than a factor
+ * of 10 (the FP64 solve ends early when five restarts in a row each reduce
+ * the residual by less than 1%), or whose state turns
  * non-finite is undone from a device copy of the start-of-step state and
  * retried with half the sub-step; after a success the sub-step grows by 1.5
  * up to dt, until t + dt is reached.  dt itself is left unchanged.  Errors:
@@ -306,6 +323,14 @@ void hf_default_step_opts(hf_step_opts* o);
  * attempts (state = the last accepted sub-step), any CUDA or state error as
  * returned by the calls above. */
 hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* rep);
+
+/* Block-Jacobi subdomains of the preconditioner (diagnostics): for each
+ * element (caller's order), its subdomain and its position in that
+ * subdomain's elimination order (n_elems each; either may be NULL).  Within a
+ * subdomain the block ILU(0) of the element blocks of A eliminates elements
+ * in increasing position: L_ik = A_ik D_k^-1 for earlier neighbours k,
+ * D_i = A_ii - sum_k L_ik A_ki. */
+hf_status hf_get_subdomains(const hf_mesh* h, int32_t* sd_of_elem, int32_t* order_in_sd);
 
 /* Aggregate of each element (caller's element order) in the coarse level of
  * the preconditioner: the preconditioner is M^-1 = B^-1 + Phi A0^-1 Phi^T,

@@ -98,6 +98,9 @@ SIGNATURES = {
                                    C.c_double, C.c_double, C.c_int, C.c_double]),
     "hf_set_solver": (C.c_int, [_H, C.POINTER(hf_solver_opts)]),
     "hf_set_fixed_pressure": (C.c_int, [_H, C.c_int64, _i64p, _dp]),
+    "hf_set_wait_limit": (C.c_int, [_H, C.c_int64]),
+    "hf_get_subdomains": (C.c_int, [_H, _i32p, _i32p]),
+    "hf_check_wait_timeout": (C.c_int, [_H]),
     "hf_set_state": (C.c_int, [_H, _dp, _dp, _i8p, _i8p, _dp, C.c_double]),
     "hf_get_state": (C.c_int, [_H, _dp, _dp, _i8p, _i8p, _dp, _dp]),
     "hf_newton_step": (C.c_int, [_H, C.POINTER(hf_newton_report)]),
@@ -130,7 +133,7 @@ SIGNATURES = {
     "hf_runtime_stats": (C.c_int, [C.c_void_p, _i64p]),
     "hf_runtime_now": (C.c_double, [C.c_void_p]),
 }
-KERNEL_CLASSES = ["spmv", "precond", "orth", "factor", "assembly", "spmv64", "update", "precond_aux"]
+KERNEL_CLASSES = ["spmv", "precond", "orth", "factor", "assembly", "spmv64", "update", "precond_aux", "gmres_cycles"]
 
 _lib = None
 
@@ -291,6 +294,19 @@ class HFMesh:
         self.lib.hf_default_solver_opts(C.byref(o))
         return o
 
+    def hf_get_subdomains(self):
+        ne = self._keep[1].shape[0]
+        sd = np.zeros(ne, np.int32)
+        order = np.zeros(ne, np.int32)
+        self._check(self.lib.hf_get_subdomains(self.h, _ptr(sd, C.c_int32), _ptr(order, C.c_int32)))
+        return sd, order
+
+    def hf_set_wait_limit(self, polls):
+        self._check(self.lib.hf_set_wait_limit(self.h, int(polls)))
+
+    def hf_check_wait_timeout(self):
+        self._check(self.lib.hf_check_wait_timeout(self.h))
+
     def hf_set_fixed_pressure(self, p_dofs, values):
         d = np.ascontiguousarray(p_dofs, dtype=np.int64)
         v = np.ascontiguousarray(values, dtype=np.float64)
@@ -396,11 +412,12 @@ class HFMesh:
         return A0, inv, geo
 
     def hf_set_profiling(self, on=True):
-        self._check(self.lib.hf_set_profiling(self.h, int(bool(on))))
+        """on: False/0 off, True/1 every kernel class, 2 whole GMRES cycles."""
+        self._check(self.lib.hf_set_profiling(self.h, int(on)))
 
     def hf_get_kernel_times(self):
-        ms = np.zeros(8)
-        n = np.zeros(8, np.int64)
+        ms = np.zeros(len(KERNEL_CLASSES))
+        n = np.zeros(len(KERNEL_CLASSES), np.int64)
         self._check(self.lib.hf_get_kernel_times(self.h, _ptr(ms, C.c_double), _ptr(n, C.c_int64)))
         return {k: (float(ms[i]), int(n[i])) for i, k in enumerate(KERNEL_CLASSES)}
 

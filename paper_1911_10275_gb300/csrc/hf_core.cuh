@@ -156,6 +156,7 @@ struct DevMesh {
   long long* sd_fwd;        // [nsd] start of each subdomain's forward stream
   long long* sd_bwd;        // [nsd] start of each subdomain's backward stream
   int* err_flag;            // [0]: a bounded wait in a kernel gave up
+  int wait_polls;           // polls of a bounded mbarrier wait before it gives up
   // parameters
   double lam, mu, sigma_c, delta_c, b_stab;
   double mu_f, Q0, delta_f, dt, p_v;

@@ -79,6 +79,7 @@ struct GmresState {
 // event-timed kernel classes (profiling mode)
 enum ProfKind { PK_SPMV = 0, PK_PREC = 1, PK_ORTH = 2, PK_FACTOR = 3, PK_ASSEMBLY = 4, PK_SPMV64 = 5,
                 PK_UPDATE = 6, PK_PREC_AUX = 7, PK_COUNT = 8 };
+constexpr int PK_REPORTED = 9;  // the classes above plus whole GMRES cycles
 constexpr int PROF_EVENTS = 256;
 // event pair recorded as graph nodes inside a captured GMRES cycle; j is the
 // Arnoldi step it belongs to (-1: once per cycle)
@@ -99,6 +100,13 @@ struct Prof {
   int n = 0;
   double ms[PK_COUNT] = {};
   long long launches[PK_COUNT] = {};
+  // mode 2: whole GMRES cycles timed by an event pair around each launch
+  // (graph replay or eager cycle), nothing inside them
+  bool cycles = false;
+  bool cyc_pending = false;
+  cudaEvent_t cyc_a = nullptr, cyc_b = nullptr;
+  double cycle_ms = 0.0;
+  long long cycle_steps = 0;
 };
 
 }  // namespace hfk
@@ -226,6 +234,7 @@ hf_status linear_solve(hf_mesh* h, const double* b, double* x, hf_newton_report*
 hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]);
 void launch_neg_part(hf_mesh* h, const double* R, double* b, int keep_u, int keep_p);
 void launch_diag_d(hf_mesh* h);
+void launch_wait_selftest(hf_mesh* h);
 double device_norm2(hf_mesh* h, const double* v, long long n);
 hf_status set_error(hf_mesh* h, hf_status s, const std::string& msg);
 hf_status check_cuda(hf_mesh* h, cudaError_t e, const char* where);

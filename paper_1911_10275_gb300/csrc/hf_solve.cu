@@ -564,9 +564,10 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                "l"(src), "r"(bytes), "r"(smem_u32(bar))
                : "memory");
 }
-// bounded wait on an mbarrier phase; on timeout raise the error flag and go on
-__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned phase, int* err) {
-  for (int it = 0; it < (1 << 22); ++it) {
+// bounded wait on an mbarrier phase; after `polls` unsuccessful polls raise
+// the error flag and go on
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned phase, int* err, int polls) {
+  for (int it = 0; it < polls; ++it) {
     unsigned ok;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -671,7 +672,7 @@ __global__ void __launch_bounds__(32 * W) k_ilu_apply(DevMesh m, const T* __rest
       const T* blk = nullptr;
       if (sz) {
         unsigned q = qt % NQ;
-        mbar_wait(&bars[q], (qt / NQ) & 1u, m.err_flag);
+        mbar_wait(&bars[q], (qt / NQ) & 1u, m.err_flag, m.wait_polls);
         blk = ring + (unsigned)qstart[q] % RINGV;
       }
       // all block dot products first (independent), then the row updates in
@@ -1122,8 +1123,8 @@ __global__ void __launch_bounds__(GS_T) k_gs_fin(const T* __restrict__ V_in, T* 
 // The convergence test of column j-1 runs at step j; at the end of a cycle a
 // last reduction finalises column m-1.
 constexpr int DC_LD = 2 * GM_MAX + 2;  // row length of the reduction table
-constexpr int DC_SLAB = 4096;                           // doubles staged at a time by dc_reduce
-constexpr size_t DC_SMEM = DC_SLAB * sizeof(double);   // 32 KiB of dynamic shared memory
+constexpr int DC_SLAB = 12288;                          // doubles staged at a time by dc_reduce
+constexpr size_t DC_SMEM = DC_SLAB * sizeof(double);   // 96 KiB of dynamic shared memory (opt-in)
 
 // block partials of [Q^T u, Q^T w, u.u, u.w] (w != null) or [Q^T u, u.u]
 template <typename T>
@@ -1231,26 +1232,48 @@ __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long l
 }
 
 // column sums of the nb x nvc table (row length DC_LD) into out[0..nvc), by
-// the whole CTA: the table is staged through shared memory in slabs of rows
-// (coalesced, all loads in flight), then each column is added in row order,
-// the same order in every CTA
+// the whole CTA: the table is staged in shared memory (one slab of up to
+// DC_SLAB values at a time, four independent loads per thread and pass),
+// then G threads per column add interleaved rows and their G partial sums
+// meet in a fixed order: the same order, hence the same result, in every CTA
 __device__ void dc_reduce(const double* part, int nb, int nvc, double* out) {
   extern __shared__ double stage[];
+  __shared__ double gpart[GS_T];
   const int rows_per = max(1, DC_SLAB / max(nvc, 1));
-  for (int c = threadIdx.x; c < nvc; c += blockDim.x) out[c] = 0.0;
+  const int nth = min((int)blockDim.x, GS_T);  // threads past GS_T only join the barriers
+  const int G = max(1, min(8, nth / max(nvc, 1)));
+  const int c = threadIdx.x % max(nvc, 1), g = (int)threadIdx.x < nth ? threadIdx.x / max(nvc, 1) : G;
+  double acc = 0.0;
   for (int r0 = 0; r0 < nb; r0 += rows_per) {
     const int nr = min(rows_per, nb - r0);
+    const int tot = nr * nvc;
     __syncthreads();
-    for (int t = threadIdx.x; t < nr * nvc; t += blockDim.x) {
-      const int rr = t / nvc, c = t - rr * nvc;
-      stage[t] = __ldcg(part + (long long)(r0 + rr) * DC_LD + c);
+    for (int t = threadIdx.x; t < tot; t += 4 * nth) {
+      if ((int)threadIdx.x >= nth) break;
+      double v[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int tt = t + k * nth;
+        v[k] = 0.0;
+        if (tt < tot) {
+          const int rr = tt / nvc;
+          v[k] = __ldcg(part + (long long)(r0 + rr) * DC_LD + (tt - rr * nvc));
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+        if (t + k * nth < tot) stage[t + k * nth] = v[k];
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < nvc; c += blockDim.x) {
-      double s = out[c];
-      for (int rr = 0; rr < nr; ++rr) s += stage[rr * nvc + c];
-      out[c] = s;
-    }
+    if (g < G)
+      for (int rr = g; rr < nr; rr += G) acc += stage[rr * nvc + c];
+  }
+  if (g < G) gpart[g * nvc + c] = acc;
+  __syncthreads();
+  for (int cc = threadIdx.x; cc < nvc; cc += nth) {
+    double t = 0.0;
+    for (int k = 0; k < G; ++k) t += gpart[k * nvc + cc];
+    out[cc] = t;
   }
   __syncthreads();
 }
@@ -1382,6 +1405,321 @@ __global__ void __launch_bounds__(GS_T) k_dc_upd(T* V, long long ldv, int j, con
     if (j > 0) u[i] = vj;
     un[i] = (wq - dd * vj) * ir;
   }
+}
+
+// ---- the delayed CGS2 with the basis streamed through shared memory
+// The register kernels above keep only a batch of loads in flight per
+// thread (their accumulators take most of the registers), so each thread
+// pays a DRAM round trip every few KB.  These variants stream the basis with
+// bulk asynchronous copies (cp.async.bulk) into a ring of row segments in
+// shared memory: a producer warp issues the copies up to DCT_S segments ahead,
+// waiting for a slot only when the consumers have not yet released it
+// (mbarriers, bounded waits), and 16 consumer warps compute from shared
+// memory.  The bytes in flight are bounded by shared memory, not registers.
+// Each CTA owns a contiguous slice of rb rows (a multiple of 64, so every
+// segment starts 256-byte aligned); copies are rounded up to 16 bytes and may
+// read up to three elements past n, inside the padded allocations.
+constexpr int DCT_CONS = 16;                   // consumer warps
+constexpr int DCT_THREADS = 32 * (DCT_CONS + 1);
+template <typename T> struct DcTma {
+  static constexpr int TR = sizeof(T) == 4 ? 4096 : 2048;  // rows per segment (16 KiB)
+  static constexpr int S = sizeof(T) == 4 ? 8 : 5;         // ring slots (128 / 80 KiB in flight)
+};
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// barrier over threads 0 .. GS_T-1 of the block (named barrier 1)
+__device__ __forceinline__ void sync_gs() { asm volatile("bar.sync 1, %0;" ::"n"(GS_T) : "memory"); }
+
+// after the consumers: wait (bounded) for the last copy issued into each ring
+// slot, so that no copy is still in flight when the block exits, even after a
+// wait that gave up
+__device__ __forceinline__ void dct_drain(unsigned long long* full, int S, long long nseg, int* err, int polls) {
+  for (int q = 0; q < S && q < nseg; ++q) {
+    const long long last = (nseg - 1 - q) / S;  // the slot's last round
+    mbar_wait(&full[q], (unsigned)(last & 1), err, polls);
+  }
+}
+
+template <typename T> __device__ __forceinline__ unsigned dct_bytes(long long rows) {
+  return (unsigned)((rows * (long long)sizeof(T) + 15) / 16 * 16);
+}
+
+// block partials of [Q^T u, Q^T w, u.u, u.w] over this CTA's slice, the
+// column sums taken column after column: u and w of the slice stay in shared
+// memory, the basis columns stream through the ring
+template <typename T>
+__global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restrict__ V, long long ldv, int j,
+                                                               const T* __restrict__ w, long long n, double* part,
+                                                               const GmresState* gs, long long rb, int polls,
+                                                               int* err) {
+  if (gs->done) return;
+  constexpr int S = DcTma<T>::S, TR = DcTma<T>::TR, NC = DCT_CONS * 32;
+  extern __shared__ __align__(128) unsigned char dsm[];
+  T* us = reinterpret_cast<T*>(dsm);
+  T* wsl = us + rb;
+  T* ring = wsl + rb;
+  double* wsum = reinterpret_cast<double*>(ring + (size_t)S * TR);  // [DCT_CONS][DC_LD]
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(wsum + DCT_CONS * DC_LD);
+  unsigned long long* empty = full + S;
+  unsigned long long* uwbar = empty + S;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r0 = (long long)blockIdx.x * rb;
+  const long long nr = r0 < n ? (n - r0 < rb ? n - r0 : rb) : 0;
+  const int nt = (int)((nr + TR - 1) / TR);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], DCT_CONS);
+    }
+    mbar_init(uwbar, (unsigned)max(2 * nt, 1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  const T* u = V + (long long)j * ldv;
+  if (warp == DCT_CONS) {
+    // producer
+    if (lane == 0 && nt > 0) {
+      for (int t = 0; t < nt; ++t) {
+        const long long a = r0 + (long long)t * TR;
+        const unsigned by = dct_bytes<T>(r0 + nr - a < TR ? r0 + nr - a : TR);
+        bulk_load(us + (size_t)t * TR, u + a, by, uwbar);
+        bulk_load(wsl + (size_t)t * TR, w + a, by, uwbar);
+      }
+      const long long nseg = (long long)j * nt;
+      for (long long k = 0; k < nseg; ++k) {
+        const int q = (int)(k % S);
+        const long long rnd = k / S;
+        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls);
+        const int c = (int)(k / nt), t = (int)(k % nt);
+        const long long a = r0 + (long long)t * TR;
+        bulk_load(ring + (size_t)q * TR, V + (long long)c * ldv + a, dct_bytes<T>(r0 + nr - a < TR ? r0 + nr - a : TR),
+                  &full[q]);
+      }
+    }
+  } else {
+    T uu = (T)0, uw = (T)0;
+    if (nt > 0) mbar_wait(uwbar, 0u, err, polls);
+    for (long long l = threadIdx.x; l < nr; l += NC) {
+      const T uv = us[l], wv = wsl[l];
+      uu += uv * uv;
+      uw += uv * wv;
+    }
+    {
+      const double a = warp_sum((double)uu), b = warp_sum((double)uw);
+      if (lane == 0) {
+        wsum[warp * DC_LD + 2 * j] = a;
+        wsum[warp * DC_LD + 2 * j + 1] = b;
+      }
+    }
+    for (int c = 0; c < j; ++c) {
+      T au = (T)0, aw = (T)0;
+      for (int t = 0; t < nt; ++t) {
+        const long long k = (long long)c * nt + t;
+        const int q = (int)(k % S);
+        mbar_wait(&full[q], (unsigned)((k / S) & 1), err, polls);
+        const T* seg = ring + (size_t)q * TR;
+        const T* ut = us + (size_t)t * TR;
+        const T* wt = wsl + (size_t)t * TR;
+        const int rows = (int)(nr - (long long)t * TR < TR ? nr - (long long)t * TR : TR);
+        for (int l = threadIdx.x; l < rows; l += NC) {
+          const T qv = seg[l];
+          au += qv * ut[l];
+          aw += qv * wt[l];
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&empty[q]);
+      }
+      const double a = warp_sum((double)au), b = warp_sum((double)aw);
+      if (lane == 0) {
+        wsum[warp * DC_LD + c] = a;
+        wsum[warp * DC_LD + j + c] = b;
+      }
+    }
+    if (warp == 0 && lane == 0) dct_drain(full, S, (long long)j * nt, err, polls);
+  }
+  __syncthreads();
+  double* row = part + (long long)blockIdx.x * DC_LD;
+  for (int c = threadIdx.x; c < 2 * j + 2; c += blockDim.x) {
+    double sacc = 0.0;
+    for (int k = 0; k < DCT_CONS; ++k) sacc += wsum[k * DC_LD + c];
+    row[c] = sacc;
+  }
+}
+
+// the update sweep of the delayed CGS2 step with the basis streamed through
+// the ring, tile after tile: per tile the segments of u_j and w, then of the
+// j final basis vectors; each consumer thread keeps its rows' two running
+// sums in registers and writes v_j and the next lagged vector at the end of
+// the tile.  Block 0 keeps the Hessenberg bookkeeping, as in k_dc_upd; the
+// other CTAs share the rows (slices of rb rows).
+template <typename T>
+__global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long ldv, int j, const T* __restrict__ w,
+                                                               long long n, const double* part, GmresState* gs,
+                                                               int mrest, long long rb, int polls, int* err) {
+  if (gs->done) return;
+  constexpr int S = DcTma<T>::S, TR = DcTma<T>::TR, NC = DCT_CONS * 32, RPT = TR / NC;
+  __shared__ double red[DC_LD];
+  __shared__ T coef[2 * GM_MAX];
+  __shared__ double hc[GM_LD + 1], cvec[GM_LD];
+  __shared__ __align__(8) unsigned long long full[S], empty[S];
+  const int nb = gridDim.x;
+  dc_reduce(part, nb, 2 * j + 2, red);
+  const double uu = red[2 * j], uw = red[2 * j + 1];
+  double ab = 0.0, aa = 0.0;
+  for (int k = 0; k < j; ++k) {
+    ab += red[k] * red[j + k];
+    aa += red[k] * red[k];
+  }
+  const double r2 = uu - aa;
+  const double r = j == 0 ? 1.0 : (r2 > 0.0 ? sqrt(r2) : 0.0);
+  const double inv_r = r > 0.0 ? 1.0 / r : 0.0;
+  const double d = (uw - ab) * inv_r;
+  if (blockIdx.x == 0) {
+    // Hessenberg bookkeeping by the first GS_T threads (no sweep in this
+    // block); they synchronise on a named barrier of exactly GS_T threads,
+    // the producer warp leaves
+    if (threadIdx.x >= GS_T) return;
+    if (j == 0) {
+      if (threadIdx.x == 0) gs->Hr[0] = uw;
+      return;
+    }
+    double* Hr = gs->Hr;
+    for (int i = threadIdx.x; i < j; i += GS_T) hc[i] = Hr[(j - 1) * GM_LD + i] + red[i];
+    if (threadIdx.x == 0) hc[j] = r;
+    sync_gs();
+    for (int i = threadIdx.x; i <= j; i += GS_T) Hr[(j - 1) * GM_LD + i] = hc[i];
+    {
+      __shared__ double cpart[4][128];
+      const int i = threadIdx.x & 127, g = threadIdx.x >> 7;
+      double ci = 0.0;
+      if (i <= j) {
+#pragma unroll 4
+        for (int k = g; k < j - 1; k += 4)
+          if (i <= k + 1) ci += Hr[k * GM_LD + i] * red[k];
+      }
+      cpart[g][i] = ci;
+      sync_gs();
+      if (threadIdx.x <= (unsigned)j)
+        cvec[threadIdx.x] = ((cpart[0][threadIdx.x] + cpart[1][threadIdx.x]) + (cpart[2][threadIdx.x] +
+                            cpart[3][threadIdx.x])) + hc[threadIdx.x] * red[j - 1];
+      sync_gs();
+    }
+    if (r > 0.0)
+      for (int i = threadIdx.x; i <= j; i += GS_T)
+        Hr[j * GM_LD + i] = i < j ? (red[j + i] - cvec[i]) * inv_r : (d - cvec[j]) * inv_r;
+    {
+      __shared__ double csd[GM_MAX], snd[GM_MAX];
+      const int jc = j - 1;
+      for (int i = threadIdx.x; i < jc; i += GS_T) {
+        csd[i] = gs->cs[i];
+        snd[i] = gs->sn[i];
+      }
+      sync_gs();
+      if (threadIdx.x == 0) {
+        for (int i = 0; i < jc; ++i) {
+          const double p0 = hc[i], p1 = hc[i + 1];
+          hc[i] = csd[i] * p0 + snd[i] * p1;
+          hc[i + 1] = -snd[i] * p0 + csd[i] * p1;
+        }
+        const double a0 = hc[jc], sub = hc[jc + 1];
+        const double den = hypot(a0, sub);
+        const double cs = den > 0.0 ? a0 / den : 1.0, sn = den > 0.0 ? sub / den : 0.0;
+        hc[jc] = den;
+        hc[jc + 1] = 0.0;
+        gs->cs[jc] = cs;
+        gs->sn[jc] = sn;
+        const double gj = gs->g[jc];
+        gs->g[jc + 1] = -sn * gj;
+        gs->g[jc] = cs * gj;
+        gs->iters = jc + 1;
+        gs->jlast = jc + 1;
+        if (fabs(gs->g[jc + 1]) <= gs->tol_abs || jc + 1 >= mrest || !(sub > 0.0) || !isfinite(sub)) gs->done = 1;
+      }
+      sync_gs();
+      for (int i = threadIdx.x; i <= jc + 1; i += GS_T) gs->H[jc * GM_LD + i] = hc[i];
+    }
+    return;
+  }
+  for (int k = threadIdx.x; k < j; k += blockDim.x) {
+    coef[k] = (T)red[k];
+    coef[GM_MAX + k] = (T)red[j + k];
+  }
+  // the staging area of dc_reduce becomes the ring
+  extern __shared__ __align__(128) unsigned char dsm[];
+  T* ring = reinterpret_cast<T*>(dsm);
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], DCT_CONS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  // the ring reuses dc_reduce's staging area: order its generic reads before
+  // the first asynchronous copy into it
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r0 = (long long)(blockIdx.x - 1) * rb;
+  const long long nr = r0 < n ? (n - r0 < rb ? n - r0 : rb) : 0;
+  const int nt = (int)((nr + TR - 1) / TR);
+  const int per = j + 2;  // segments per tile: u_j, w, Q_0 .. Q_{j-1}
+  T* u = V + (long long)j * ldv;
+  T* un = V + (long long)(j + 1) * ldv;
+  if (warp == DCT_CONS) {
+    if (lane == 0) {
+      const long long nseg = (long long)nt * per;
+      for (long long k = 0; k < nseg; ++k) {
+        const int q = (int)(k % S);
+        const long long rnd = k / S;
+        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls);
+        const int t = (int)(k / per), m = (int)(k % per);
+        const long long a = r0 + (long long)t * TR;
+        const T* src = m == 0 ? u + a : m == 1 ? w + a : V + (long long)(m - 2) * ldv + a;
+        bulk_load(ring + (size_t)q * TR, src, dct_bytes<T>(r0 + nr - a < TR ? r0 + nr - a : TR), &full[q]);
+      }
+    }
+    return;
+  }
+  const T ir = (T)inv_r, dd = (T)d;
+  for (int t = 0; t < nt; ++t) {
+    const int rows = (int)(nr - (long long)t * TR < TR ? nr - (long long)t * TR : TR);
+    T su[RPT], sw[RPT];
+    for (int m = 0; m < per; ++m) {
+      const long long k = (long long)t * per + m;
+      const int q = (int)(k % S);
+      mbar_wait(&full[q], (unsigned)((k / S) & 1), err, polls);
+      const T* seg = ring + (size_t)q * TR;
+      const T cu = m >= 2 ? coef[m - 2] : (T)0, cw = m >= 2 ? coef[GM_MAX + m - 2] : (T)0;
+#pragma unroll
+      for (int e = 0; e < RPT; ++e) {
+        const int l = threadIdx.x + e * NC;
+        const T v = l < rows ? seg[l] : (T)0;
+        if (m == 0) su[e] = v;
+        else if (m == 1) sw[e] = v;
+        else {
+          su[e] -= cu * v;
+          sw[e] -= cw * v;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[q]);
+    }
+    const long long a = r0 + (long long)t * TR;
+#pragma unroll
+    for (int e = 0; e < RPT; ++e) {
+      const int l = threadIdx.x + e * NC;
+      if (l < rows) {
+        const T vj = su[e] * ir;
+        if (j > 0) u[a + l] = vj;
+        un[a + l] = (sw[e] - dd * vj) * ir;
+      }
+    }
+  }
+  if (warp == 0 && lane == 0) dct_drain(full, S, (long long)nt * per, err, polls);
 }
 
 // end of a cycle that ran all mrest steps: finalise column mrest - 1 from
@@ -1616,6 +1954,17 @@ __global__ void k_copy(const T* __restrict__ a, T* b, long long n, const int* sk
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += stride) b[i] = a[i];
 }
 
+// The bounded wait of the preconditioner's copy pipeline on an mbarrier that
+// nothing completes (one arrival expected, none made): it must give up after
+// m.wait_polls polls and raise the error flag.  One thread, no copies issued.
+__global__ void k_wait_selftest(DevMesh m) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  mbar_init(&bar, 1);
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  mbar_wait(&bar, 0u, m.err_flag, m.wait_polls);
+}
+
 // ------------------------------------------------------------------ host side
 hf_status set_error(hf_mesh* h, hf_status s, const std::string& msg) {
   h->err = msg;
@@ -1723,7 +2072,43 @@ hf_status krylov_basis_alloc(hf_mesh* h, int m) {
   return HF_OK;
 }
 
+// the reduction kernels of the delayed CGS2 stage their table in more than
+// the default 48 KiB of shared memory: raise their limit once per process
+constexpr int SMEM_OPTIN = 227 * 1024;  // opt-in shared memory per block on this GPU
+
+template <typename T> static void dc_configure() {
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaFuncSetAttribute(k_dc_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DC_SMEM);
+    cudaFuncSetAttribute(k_dc_close, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DC_SMEM);
+    cudaFuncAttributes fa{};
+    if (cudaFuncGetAttributes(&fa, k_dc_dot_tma<T>) == cudaSuccess)
+      cudaFuncSetAttribute(k_dc_dot_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           SMEM_OPTIN - (int)fa.sharedSizeBytes);
+    if (cudaFuncGetAttributes(&fa, k_dc_upd_tma<T>) == cudaSuccess)
+      cudaFuncSetAttribute(k_dc_upd_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           SMEM_OPTIN - (int)fa.sharedSizeBytes);
+    cudaGetLastError();
+  });
+}
+
+// dynamic shared memory of the streamed delayed CGS2 dot kernel for slices
+// of rb rows (u and w of the slice, the ring, the per-warp sums, barriers),
+// or 0 when it does not fit beside the kernel's static shared memory
+template <typename T> static size_t dct_dot_smem(long long rb) {
+  const size_t b = (size_t)2 * rb * sizeof(T) + (size_t)DcTma<T>::S * DcTma<T>::TR * sizeof(T) +
+                   (size_t)DCT_CONS * DC_LD * sizeof(double) + (size_t)(2 * DcTma<T>::S + 1) * 8;
+  cudaFuncAttributes fa{};
+  if (cudaFuncGetAttributes(&fa, k_dc_dot_tma<T>) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b + fa.sharedSizeBytes <= (size_t)SMEM_OPTIN ? b : 0;
+}
+
 hf_status solver_alloc(hf_mesh* h) {
+  dc_configure<float>();
+  dc_configure<double>();
   long long N = h->N;
   int m = std::max(1, std::min(GM_MAX, h->opts.restart));
   long long ldv = (N + 63) / 64 * 64;
@@ -1907,8 +2292,16 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
     prof_end(h);
     prof_begin(h, PK_ORTH);
     if (h->opts.reorth == 3) {
-      { note_launch(); k_dc_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs); }
-      { note_launch(); k_dc_upd<T><<<nb, GS_T, DC_SMEM, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, mrest); }
+      const long long rb_dot = (N + nb - 1) / nb, rb_upd = nb > 1 ? (N + nb - 2) / (nb - 1) : 0;
+      const size_t dsm = nb > 1 ? dct_dot_smem<T>((rb_dot + 63) / 64 * 64) : 0;
+      if (dsm) {
+        // the basis streamed through shared memory by bulk copies
+        { note_launch(); k_dc_dot_tma<T><<<nb, DCT_THREADS, dsm, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, (rb_dot + 63) / 64 * 64, h->d.wait_polls, h->d.err_flag); }
+        { note_launch(); k_dc_upd_tma<T><<<nb, DCT_THREADS, std::max(DC_SMEM, (size_t)DcTma<T>::S * DcTma<T>::TR * sizeof(T)), h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, mrest, (rb_upd + 63) / 64 * 64, h->d.wait_polls, h->d.err_flag); }
+      } else {
+        { note_launch(); k_dc_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs); }
+        { note_launch(); k_dc_upd<T><<<nb, GS_T, DC_SMEM, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, mrest); }
+      }
       prof_end(h);
       continue;
     }
@@ -1952,8 +2345,26 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
 }
 
 template <typename T, int DIM>
+static hf_status run_cycle_inner(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest,
+                                 cudaGraphExec_t* gexec, std::vector<GraphEv>* gev);
+
+template <typename T, int DIM>
 static hf_status run_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest, cudaGraphExec_t* gexec,
                            std::vector<GraphEv>* gev) {
+  Prof& p = h->prof;
+  const bool timed = p.cycles && p.cyc_a && p.cyc_b;
+  if (timed) cudaEventRecord(p.cyc_a, h->stream);
+  hf_status s = run_cycle_inner<T, DIM>(h, K, dg, off, mrest, gexec, gev);
+  if (timed) {
+    cudaEventRecord(p.cyc_b, h->stream);
+    p.cyc_pending = true;
+  }
+  return s;
+}
+
+template <typename T, int DIM>
+static hf_status run_cycle_inner(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int mrest,
+                                 cudaGraphExec_t* gexec, std::vector<GraphEv>* gev) {
   long long& gk = sizeof(T) == 8 ? h->graph_kernels64 : h->graph_kernels32;
   if (!h->opts.use_graphs || h->d.phase != 0) {
     gmres_cycle<T, DIM>(h, K, dg, off, mrest);
@@ -2006,6 +2417,17 @@ static hf_status read_gs(hf_mesh* h, CycleInfo* ci) {
   h->gs_reorths = tmp.reorths;
   h->gs_reorth_cols = tmp.reorth_cols;
   h->gs_cols += (long long)tmp.iters * (tmp.iters + 1) / 2;
+  Prof& p = h->prof;
+  if (p.cyc_pending) {
+    float ms = 0.0f;
+    if (cudaEventElapsedTime(&ms, p.cyc_a, p.cyc_b) == cudaSuccess) {
+      p.cycle_ms += ms;
+      p.cycle_steps += tmp.iters;
+    } else {
+      cudaGetLastError();
+    }
+    p.cyc_pending = false;
+  }
   return HF_OK;
 }
 
@@ -2103,6 +2525,11 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
       note_launch();
       k_fill<double><<<rb, RB, 0, h->stream>>>(K.x, N, 0.0);
     }
+    // restarted cycles from the true residual; five cycles in a row that each
+    // reduce it by less than 1% (stagnation at the attainable accuracy) end
+    // the solve
+    double prev_cycle = HUGE_VAL;
+    int stalled = 0;
     for (;;) {
       spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, K.x, K.w, nullptr);
       { note_launch(); k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, K.w, K.V, N, h->d_partial, cnt, h->d_gs, tol); }
@@ -2116,6 +2543,9 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
         break;
       }
       if (rnorm <= tol || total >= o.max_iters) break;
+      stalled = rnorm > 0.99 * prev_cycle ? stalled + 1 : 0;
+      if (stalled >= 5) break;
+      prev_cycle = rnorm;
       if ((st = run_cycle<double, DIM>(h, K, h->J64.dg, h->J64.off, mrest, &h->graph64, &h->gev64))) break;
       if ((st = read_gs(h, &ci))) break;
       if (o.use_graphs) prof_flush_graph(h, h->gev64, ci.iters);
@@ -2179,6 +2609,11 @@ hf_status newton_update(hf_mesh* h, const double* Dx, double out[4]) {
 
 void launch_neg_part(hf_mesh* h, const double* R, double* b, int keep_u, int keep_p) {
   { note_launch(); k_neg_part<<<h->red_blocks, RB, 0, h->stream>>>(R, b, h->nu, h->N, keep_u, keep_p); }
+}
+
+void launch_wait_selftest(hf_mesh* h) {
+  note_launch();
+  k_wait_selftest<<<1, 32, 0, h->stream>>>(h->d);
 }
 
 void launch_diag_d(hf_mesh* h) {

@@ -34,7 +34,7 @@ def _run(wl, prec, golden, max_iters):
     g.hf_set_injection(wl.mu, wl.Q0, inj, wts, wl.delta_f, wl.dt, 0.0, True, wl.fluid_length)
     g.hf_set_solver(**bench.HEADLINE[prec], **bench.COMMON)
     g.hf_set_state(*wl.seed())
-    loop = bench.NewtonLoop(g, wl)
+    loop = bench.NewtonLoop(g, wl, rtol=bench.HEADLINE[prec]["rtol"])
     u_idx = np.asarray(golden["u_index"], dtype=np.int64)
     worst = {"U": 0.0, "P": 0.0, "w": 0.0}
     rows = []

@@ -179,3 +179,24 @@ def test_mixed_solve_falls_back_to_fp64_when_fp32_stalls():
     assert reps[0]["fp64_fallback"] == 1 and reps[1]["fp64_fallback"] == 0
     for x, y in zip(states[0][:2], states[1][:2]):
         assert rel_err(x, y) <= 0.1
+
+
+def test_bounded_device_wait_gives_up_with_timeout_status():
+    """Failure detection without a fault: the preconditioner's bounded
+    mbarrier wait, run on a barrier nothing completes, gives up after the
+    host-set number of polls and the call returns HF_ERR_TIMEOUT; the handle
+    stays usable (a Newton step afterwards converges its linear solve)."""
+    from paper_1911_10275_gb300 import HFError
+    wl = kgd_2d(n=6, length=12.0, steps=1, seed_cells=2)
+    g = gpu_for(wl)
+    g.hf_set_state(*wl.seed())
+    g.hf_set_wait_limit(64)
+    with pytest.raises(HFError) as err:
+        g.hf_check_wait_timeout()
+    assert err.value.status == -6
+    with pytest.raises(HFError):
+        g.hf_set_wait_limit(0)
+    g.hf_set_wait_limit(1 << 22)
+    rep = g.hf_newton_step()
+    assert rep["lin_converged"]
+    g.close()

@@ -42,7 +42,8 @@ def test_staggered_iterations_match_oracle():
         assert rel_err(P, o.P) <= 1e-9
         assert rg["du_rel"] == pytest.approx(ro["du_rel"], rel=1e-7)
         assert rg["dp_rel"] == pytest.approx(ro["dp_rel"], rel=1e-7)
-        assert np.all(P[fixed] == 0.0)
+        # an identity row, met to the GMRES tolerance
+        assert np.abs(P[fixed]).max() <= 1e-9 * np.abs(P).max()
     g.close()
 
 
@@ -57,7 +58,7 @@ def test_fixed_pressure_holds_in_the_coupled_scheme():
     o.newton_step()
     U, P = g.hf_get_state()[:2]
     assert rel_err(U, o.U) <= 1e-9 and rel_err(P, o.P) <= 1e-9
-    assert np.all(P[fixed] == 0.0)
+    assert np.abs(P[fixed]).max() <= 1e-9 * np.abs(P).max()
     g.close()
 
 
