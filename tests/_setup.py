@@ -51,7 +51,7 @@ def rel_err(a, b):
     return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
 
 
-def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=None):
+def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=None, log=None):
     """One time step of Sec. 3 on the oracle, with the driver rules of
     hf_advance_step: Newton until converged, the criterion, Newton again if it
     switched facets (at most rounds_max rounds), end of step; an attempt that
@@ -61,7 +61,10 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
     failures in a row, 256 attempts in all.  Past newton_max an attempt goes
     on while the increments at least halve every iteration (at most
     4 newton_max iterations).  ``newton()`` replaces ``o.newton_step()``
-    (the same iteration with pooled assembly, say)."""
+    (the same iteration with pooled assembly, say).  With ``log`` a list, one
+    record per attempt is appended: its sub-step, the Newton iterations of
+    each Newton round (a round ends with the fracture criterion), the facets
+    each criterion switched, and whether the attempt was accepted."""
     newton = newton or o.newton_step
     dt0 = o.prm.dt
     target = o.t + dt0
@@ -77,6 +80,7 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
         sub = min(sub, target - o.t)
         o.prm.dt = sub
         ok, rounds, it, prev = False, 0, 0, np.inf
+        rec = {"dt": sub, "rounds": [], "switched": [], "accepted": False}
         while True:
             r = newton()
             rep["newton_iters"] += 1
@@ -86,6 +90,8 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
             if r["converged"]:
                 n_new, _ = o.check_fracture_criterion()
                 rounds += 1
+                rec["rounds"].append(it)
+                rec["switched"].append(int(n_new))
                 if n_new == 0 or rounds >= rounds_max:
                     ok = True
                     break
@@ -96,6 +102,11 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
                 break
             prev = inc
         attempts += 1
+        if not ok:
+            rec["rounds"].append(it)
+        rec["accepted"] = ok
+        if log is not None:
+            log.append(rec)
         if ok:
             o.accept_step()
             rep["substeps"] += 1

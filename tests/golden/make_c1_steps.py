@@ -12,6 +12,9 @@ over a process pool.  Only oracle/, the oracle's driver in tests/_setup.py
 and the seeded input generator are used.
 
 Stored per step: the step report (Newton iterations, cutbacks, sub-steps),
+the attempt log (sub-step, Newton iterations per round, facets switched by
+each criterion, accepted or undone) from which a caller can replay the
+oracle's decisions,
 facet-state counts and lists, U at a fixed sample of unknowns, every
 non-zero pressure, the openings at the face nodes of every cohesive or fluid
 facet, and the infinity norms of the full fields.
@@ -69,11 +72,12 @@ def main():
 
     for k in range(1, args.steps + 1):
         t0 = time.time()
-        rep = oracle_advance_step(o, newton=newton)
+        log = []
+        rep = oracle_advance_step(o, newton=newton, log=log)
         wf = o.opening_at_face_nodes(o.U)
         faces = np.nonzero(m.face_crackable & ((o.alpha > 0) | (o.beta > 0)))[0]
         p_idx = np.nonzero(o.P != 0.0)[0]
-        out["steps"].append({"k": k, "t": o.t, **{key: int(v) for key, v in rep.items()},
+        out["steps"].append({"k": k, "t": o.t, **{key: int(v) for key, v in rep.items()}, "attempts": log,
                              "alpha_faces": np.nonzero(o.alpha)[0].tolist(),
                              "beta_faces": np.nonzero(o.beta)[0].tolist(),
                              "U": o.U[u_idx].tolist(), "P_index": p_idx.tolist(), "P": o.P[p_idx].tolist(),
