@@ -42,9 +42,11 @@ def dist_env():
 
 
 def workload(name):
-    from hf_inputs import c3_penny, kgd_2d, penny_3d
+    from hf_inputs import c2_kgd_viscosity, c3_penny, kgd_2d, penny_3d
     if name == "c3":
         return c3_penny()
+    if name == "c2":
+        return c2_kgd_viscosity()
     if name == "small3d":
         return penny_3d(n=6, name="penny3d_n6")
     if name == "c1":

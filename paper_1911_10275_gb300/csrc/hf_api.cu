@@ -1496,7 +1496,7 @@ hf_status hf_estimate_device_bytes(const hf_mesh_desc* desc, const hf_solver_opt
     int cA = 0, cnagg = 0, cnc = 0;
     coarse_sizes(ne, (int)dim, o.coarse ? o.coarse_max : 2048, &cA, &cnagg, &cnc);
     const long long nc2 = (long long)cnc * cnc;
-    add(cnagg * 4 * 8); add(nu * 8); add(nu * 4); add(nc2 * 8); add(nc2 * 8); add(nc2 * 4); add(8);
+    add(cnagg * 4 * 8); add(nu * 8); add(nu * 4); add(nc2 * 8); add((long long)coarse_spare_doubles((int)cnc) * 8); add(nc2 * 4); add(8);
     add(cnc * 8); add(cnc * 8); add(cnc * 4); add(cnc * 4);
   }
   // time-step snapshot

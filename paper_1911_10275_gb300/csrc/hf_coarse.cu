@@ -205,26 +205,122 @@ __global__ void k_coarse_thresh(const double* A0, int nc, double* thr) {
   if (threadIdx.x == 0) *thr = 1e-12 * red[0];
 }
 
-// one Gauss-Jordan step of the in-place inversion, from X into Y.  A pivot at
-// or below the threshold (a mode the linear operator does not constrain, e.g.
-// a piece cut free by cracks) drops that mode: its row and column become 0.
-__global__ void k_gj_step(const double* __restrict__ X, double* __restrict__ Y, int nc, int k,
-                          const double* __restrict__ thr) {
-  long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= (long long)nc * nc) return;
-  int i = (int)(idx / nc), j = (int)(idx % nc);
-  double p = X[(long long)k * nc + k];
-  double out;
-  if (!(fabs(p) > *thr)) {
-    out = (i == k || j == k) ? 0.0 : X[idx];
-  } else {
-    double piv = 1.0 / p;
-    if (i == k && j == k) out = piv;
-    else if (i == k) out = X[idx] * piv;
-    else if (j == k) out = -X[idx] * piv;
-    else out = X[idx] - X[(long long)i * nc + k] * X[(long long)k * nc + j] * piv;
+// Blocked Gauss-Jordan inversion in place, GJB pivots per pass.  The pivots
+// are taken in the natural order; a pivot at or below the threshold (a mode
+// the linear operator does not constrain, e.g. a piece cut free by cracks)
+// drops that mode: its row and column of the result are 0, as if the index
+// were deleted from the matrix.  For the pivot set K and the rest R, with
+// P = X[K,K]^+ the pivot block inverted by the same elementwise steps:
+//   X[K,K] <- P,   X[K,R] <- P X[K,R],   X[R,K] <- -X[R,K] P,
+//   X[R,R] <- X[R,R] - X[R,K] P X[K,R].
+constexpr int GJB = 32;   // pivots per pass
+constexpr int GJT = 64;   // output tile of the update (GJT x GJT per CTA)
+
+// P = X[K,K]^+ by GJB x GJB threads, one element each, the pivots in order
+__global__ void __launch_bounds__(GJB * GJB) k_gj_pivot(const double* __restrict__ X, int nc, int k0, int kb,
+                                                        const double* __restrict__ thr, double* __restrict__ P) {
+  __shared__ double a[GJB][GJB + 1];
+  const int l = threadIdx.x / GJB, m = threadIdx.x % GJB;
+  const bool in = l < kb && m < kb;
+  a[l][m] = in ? X[(long long)(k0 + l) * nc + k0 + m] : 0.0;
+  __syncthreads();
+  const double t = *thr;
+  for (int k = 0; k < kb; ++k) {
+    const double p = a[k][k], xik = a[l][k], xkj = a[k][m], xij = a[l][m];
+    __syncthreads();
+    double out;
+    if (!(fabs(p) > t)) {
+      out = (l == k || m == k) ? 0.0 : xij;
+    } else {
+      const double piv = 1.0 / p;
+      if (l == k && m == k) out = piv;
+      else if (l == k) out = xkj * piv;
+      else if (m == k) out = -xik * piv;
+      else out = xij - xik * xkj * piv;
+    }
+    if (in) a[l][m] = out;
+    __syncthreads();
   }
-  Y[idx] = out;
+  if (in) P[l * GJB + m] = a[l][m];
+}
+
+// panel of the pass: W[i,:] = X[i,K] P for rows outside K and -P[i-k0,:] for
+// rows inside, one warp per row (lane = column of P); B = X[K,:] copied so
+// that the update can overwrite X in place
+__global__ void __launch_bounds__(256) k_gj_panel(const double* __restrict__ X, int nc, int k0, int kb,
+                                                  const double* __restrict__ P, double* __restrict__ W,
+                                                  double* __restrict__ B) {
+  __shared__ double ps[GJB][GJB];
+  for (int e = threadIdx.x; e < GJB * GJB; e += blockDim.x) ps[e / GJB][e % GJB] = P[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int i = blockIdx.x * 8 + (threadIdx.x >> 5);
+  if (i < nc) {
+    double w = 0.0;
+    if (i >= k0 && i < k0 + kb) {
+      w = lane < kb ? -ps[i - k0][lane] : 0.0;
+    } else {
+      const double x = lane < kb ? X[(long long)i * nc + k0 + lane] : 0.0;
+      for (int l = 0; l < kb; ++l) w += __shfl_sync(0xffffffffu, x, l) * ps[l][lane];
+      if (lane >= kb) w = 0.0;
+    }
+    W[(long long)i * GJB + lane] = w;
+  }
+  const long long nb = (long long)kb * nc;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < nb; e += (long long)gridDim.x * blockDim.x)
+    B[e] = X[(long long)(k0 + e / nc) * nc + e % nc];
+}
+
+// the rank-kb update of the pass over GJT x GJT tiles: every element is read
+// and written by the thread that owns it, W and B are separate buffers
+__global__ void __launch_bounds__(256) k_gj_update(double* __restrict__ X, int nc, int k0, int kb,
+                                                   const double* __restrict__ W, const double* __restrict__ B) {
+  __shared__ double wt[GJT][GJB + 1];
+  __shared__ double bt[GJB][GJT];
+  const int i0 = blockIdx.y * GJT, j0 = blockIdx.x * GJT;
+  for (int e = threadIdx.x; e < GJT * GJB; e += blockDim.x) {
+    const int r = e / GJB, m = e % GJB;
+    wt[r][m] = i0 + r < nc ? W[(long long)(i0 + r) * GJB + m] : 0.0;
+  }
+  for (int e = threadIdx.x; e < GJB * GJT; e += blockDim.x) {
+    const int m = e / GJT, c = e % GJT;
+    bt[m][c] = (m < kb && j0 + c < nc) ? B[(long long)m * nc + j0 + c] : 0.0;
+  }
+  __syncthreads();
+  const int ty = threadIdx.x >> 4, tx = threadIdx.x & 15;
+  double acc[4][4] = {};
+#pragma unroll 8
+  for (int m = 0; m < GJB; ++m) {
+    double a[4], b[4];
+#pragma unroll
+    for (int r = 0; r < 4; ++r) a[r] = wt[ty + 16 * r][m];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) b[c] = bt[m][tx + 16 * c];
+#pragma unroll
+    for (int r = 0; r < 4; ++r)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) acc[r][c] += a[r] * b[c];
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r) {
+    const int i = i0 + ty + 16 * r;
+    if (i >= nc) continue;
+    const bool ik = i >= k0 && i < k0 + kb;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int j = j0 + tx + 16 * c;
+      if (j >= nc) continue;
+      double* xp = X + (long long)i * nc + j;
+      if (j >= k0 && j < k0 + kb) *xp = -wt[ty + 16 * r][j - k0];
+      else *xp = (ik ? 0.0 : *xp) - acc[r][c];
+    }
+  }
+}
+
+// the second nc x nc buffer also holds the pivot block, the panel and the
+// copied pivot rows of the blocked inversion
+size_t coarse_spare_doubles(int nc) {
+  return std::max((size_t)nc * nc, (size_t)GJB * GJB + (size_t)2 * nc * GJB);
 }
 
 __global__ void k_coarse_to_f(const double* __restrict__ a, float* __restrict__ b, long long n) {
@@ -239,35 +335,46 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(RESTRICT_THREADS) k_coarse_restrict(DevMesh m, int A, const T* __restrict__ rc,
                                                                       const T* __restrict__ r, T* __restrict__ cc,
                                                                       const int* skip) {
-  constexpr int NED = Shape<DIM>::ned, NM = n_modes<DIM>(), NT = RESTRICT_THREADS;
-  __shared__ T red[NM][NT];
+  // one thread per element node of the aggregate: its coordinates are read
+  // once for its DIM unknowns; warp sums, then the warps' sums in order
+  constexpr int NED = Shape<DIM>::ned, NEN = Shape<DIM>::nen, NM = n_modes<DIM>(), NT = RESTRICT_THREADS;
+  constexpr int NW = NT / 32;
+  __shared__ T red[NM][NW];
   if (skip && *skip) return;
   const int g = blockIdx.x, t = threadIdx.x;
-  const long long i0 = (long long)g * A * NED, i1 = (long long)min(m.ne, (g + 1) * A) * NED;
+  const long long q0 = (long long)g * A * NEN, q1 = (long long)min(m.ne, (g + 1) * A) * NEN;
   T s[NM];
 #pragma unroll
   for (int k = 0; k < NM; ++k) s[k] = (T)0;
-  for (long long i = i0 + t; i < i1; i += NT) {
-    const int e = (int)(i / NED), c = (int)(i % NED);
-    if ((m.dirmask[e] >> c) & 1u) continue;
-    T X[DIM];
-    const long long nb = (long long)e * NED + (c / DIM) * DIM;
+  for (long long q = q0 + t; q < q1; q += NT) {
+    const int e = (int)(q / NEN), a = (int)(q - (long long)e * NEN);
+    const unsigned dm = m.dirmask[e];
+    const long long nb = (long long)e * NED + a * DIM;
+    T X[DIM], v[DIM];
 #pragma unroll
-    for (int k = 0; k < DIM; ++k) X[k] = rc[nb + k];
-    const T v = r[i];
+    for (int k = 0; k < DIM; ++k) {
+      X[k] = rc[nb + k];
+      v[k] = ((dm >> (a * DIM + k)) & 1u) ? (T)0 : r[nb + k];
+    }
 #pragma unroll
-    for (int k = 0; k < NM; ++k) s[k] += rbm<DIM>(k, c % DIM, X) * v;
+    for (int comp = 0; comp < DIM; ++comp)
+#pragma unroll
+      for (int k = 0; k < NM; ++k) s[k] += rbm<DIM>(k, comp, X) * v[comp];
   }
 #pragma unroll
-  for (int k = 0; k < NM; ++k) red[k][t] = s[k];
+  for (int k = 0; k < NM; ++k) {
+    T x = s[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((t & 31) == 0) red[k][t >> 5] = x;
+  }
   __syncthreads();
-  for (int o = NT / 2; o > 0; o >>= 1) {
-    if (t < o)
+  if (t < NM) {
+    T x = (T)0;
 #pragma unroll
-      for (int k = 0; k < NM; ++k) red[k][t] += red[k][t + o];
-    __syncthreads();
+    for (int w = 0; w < NW; ++w) x += red[t][w];
+    cc[g * NM + t] = x;
   }
-  if (t < NM) cc[g * NM + t] = red[t][0];
 }
 
 // y = A0^-1 c, one warp per row
@@ -278,17 +385,35 @@ __global__ void k_coarse_gemv(const T* __restrict__ Ainv, int nc, const T* __res
   const int row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (row >= nc) return;
   const T* a = Ainv + (long long)row * nc;
-  // four independent partial sums keep four loads in flight per lane
-  T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
-  int j = lane;
-  for (; j + 96 < nc; j += 128) {
-    s0 += a[j] * cc[j];
-    s1 += a[j + 32] * cc[j + 32];
-    s2 += a[j + 64] * cc[j + 64];
-    s3 += a[j + 96] * cc[j + 96];
+  T s;
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n;
+  if (nc % VN == 0) {
+    // rows start on 16-byte boundaries: 16-byte loads, two independent sums
+    const VT* a4 = reinterpret_cast<const VT*>(a);
+    const VT* c4 = reinterpret_cast<const VT*>(cc);
+    const int nv = nc / VN;
+    VT s0 = Vec<T>::zero(), s1 = Vec<T>::zero();
+    int j = lane;
+    for (; j + 32 < nv; j += 64) {
+      Vec<T>::madd(s0, a4[j], c4[j]);
+      Vec<T>::madd(s1, a4[j + 32], c4[j + 32]);
+    }
+    for (; j < nv; j += 32) Vec<T>::madd(s0, a4[j], c4[j]);
+    s = Vec<T>::hsum(s0) + Vec<T>::hsum(s1);
+  } else {
+    // four independent partial sums keep four loads in flight per lane
+    T s0 = (T)0, s1 = (T)0, s2 = (T)0, s3 = (T)0;
+    int j = lane;
+    for (; j + 96 < nc; j += 128) {
+      s0 += a[j] * cc[j];
+      s1 += a[j + 32] * cc[j + 32];
+      s2 += a[j + 64] * cc[j + 64];
+      s3 += a[j + 96] * cc[j + 96];
+    }
+    for (; j < nc; j += 32) s0 += a[j] * cc[j];
+    s = (s0 + s1) + (s2 + s3);
   }
-  for (; j < nc; j += 32) s0 += a[j] * cc[j];
-  T s = (s0 + s1) + (s2 + s3);
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) cy[row] = s;
@@ -351,7 +476,7 @@ hf_status coarse_layout(hf_mesh* h) {
   h->rc64 = static_cast<double*>(dev_alloc(h, nrc * sizeof(double)));
   h->rc32 = static_cast<float*>(dev_alloc(h, nrc * sizeof(float)));
   h->A0a = static_cast<double*>(dev_alloc(h, nc2 * sizeof(double)));
-  h->A0b = static_cast<double*>(dev_alloc(h, nc2 * sizeof(double)));
+  h->A0b = static_cast<double*>(dev_alloc(h, coarse_spare_doubles(nc) * sizeof(double)));
   h->A0inv32 = static_cast<float*>(dev_alloc(h, nc2 * sizeof(float)));
   h->d_cthr = static_cast<double*>(dev_alloc(h, sizeof(double)));
   h->K64.cc = static_cast<double*>(dev_alloc(h, (size_t)nc * sizeof(double)));
@@ -391,14 +516,23 @@ hf_status coarse_refactor(hf_mesh* h) {
   }
   note_launch();
   k_coarse_thresh<<<1, 256, 0, h->stream>>>(h->A0a, nc, h->d_cthr);
+  // blocked Gauss-Jordan in place on A0a; A0b holds the pivot block, the
+  // panel W (nc x GJB) and the copied pivot rows B (GJB x nc)
   double* X = h->A0a;
-  double* Y = h->A0b;
-  const unsigned blocks = (unsigned)((nc2 + 255) / 256);
-  for (int k = 0; k < nc; ++k) {
+  double* P = h->A0b;
+  double* W = P + GJB * GJB;
+  double* B = W + (size_t)nc * GJB;
+  const dim3 tiles((unsigned)((nc + GJT - 1) / GJT), (unsigned)((nc + GJT - 1) / GJT));
+  for (int k0 = 0; k0 < nc; k0 += GJB) {
+    const int kb = std::min(GJB, nc - k0);
     note_launch();
-    k_gj_step<<<blocks, 256, 0, h->stream>>>(X, Y, nc, k, h->d_cthr);
-    std::swap(X, Y);
+    k_gj_pivot<<<1, GJB * GJB, 0, h->stream>>>(X, nc, k0, kb, h->d_cthr, P);
+    note_launch();
+    k_gj_panel<<<(unsigned)((nc + 7) / 8), 256, 0, h->stream>>>(X, nc, k0, kb, P, W, B);
+    note_launch();
+    k_gj_update<<<tiles, 256, 0, h->stream>>>(X, nc, k0, kb, W, B);
   }
+  const unsigned blocks = (unsigned)((nc2 + 255) / 256);
   h->A0inv64 = X;
   note_launch();
   k_coarse_to_f<<<blocks, 256, 0, h->stream>>>(X, h->A0inv32, nc2);

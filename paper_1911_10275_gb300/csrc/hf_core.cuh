@@ -279,4 +279,36 @@ __device__ __forceinline__ void tsl(double w, double sc, double dc, double kp, d
   }
 }
 
+// 16-byte vectors for the Krylov kernels: 4 floats or 2 doubles per load
+template <typename T> struct Vec;
+template <> struct Vec<float> {
+  using type = float4;
+  static constexpr int n = 4;
+  __device__ static float dot(const float4& a, const float4& b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
+  __device__ static void axpy(float4& y, float a, const float4& x) {
+    y.x -= a * x.x; y.y -= a * x.y; y.z -= a * x.z; y.w -= a * x.w;
+  }
+  __device__ static void fma(float4& y, float a, const float4& x) {
+    y.x += a * x.x; y.y += a * x.y; y.z += a * x.z; y.w += a * x.w;
+  }
+  __device__ static float4 scale(const float4& x, float a) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
+  __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+  // y += a * b componentwise; the components summed in a fixed order
+  __device__ static void madd(float4& y, const float4& a, const float4& b) {
+    y.x += a.x * b.x; y.y += a.y * b.y; y.z += a.z * b.z; y.w += a.w * b.w;
+  }
+  __device__ static float hsum(const float4& a) { return (a.x + a.y) + (a.z + a.w); }
+};
+template <> struct Vec<double> {
+  using type = double2;
+  static constexpr int n = 2;
+  __device__ static double dot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
+  __device__ static void axpy(double2& y, double a, const double2& x) { y.x -= a * x.x; y.y -= a * x.y; }
+  __device__ static void fma(double2& y, double a, const double2& x) { y.x += a * x.x; y.y += a * x.y; }
+  __device__ static double2 scale(const double2& x, double a) { return make_double2(a * x.x, a * x.y); }
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+  __device__ static void madd(double2& y, const double2& a, const double2& b) { y.x += a.x * b.x; y.y += a.y * b.y; }
+  __device__ static double hsum(const double2& a) { return a.x + a.y; }
+};
+
 }  // namespace hfk

@@ -196,8 +196,8 @@ struct hf_mesh {
   double* agg_geo = nullptr;                // [g*4]: centre (dim), size
   double* rc64 = nullptr;                   // [e*ned + t]: scaled coordinate k of the node of slot t
   float* rc32 = nullptr;
-  double* A0a = nullptr;                    // nc x nc, Gauss-Jordan ping-pong buffers
-  double* A0b = nullptr;
+  double* A0a = nullptr;                    // nc x nc: A0, inverted in place
+  double* A0b = nullptr;                    // work of the blocked inversion; a spare copy of A0
   double* A0inv64 = nullptr;                // the buffer holding A0^-1
   float* A0inv32 = nullptr;
   double* d_cthr = nullptr;                 // pivot threshold
@@ -219,6 +219,7 @@ void dev_free(hf_mesh* h, void* p);
 void coarse_sizes(long long ne, int dim, int coarse_max, int* A, int* nagg, int* nc);
 hf_status coarse_layout(hf_mesh* h);
 hf_status coarse_refactor(hf_mesh* h);
+size_t coarse_spare_doubles(int nc);
 hf_status coarse_rebuild_copy(hf_mesh* h, double* A0_host, double* inv_host, double* geo_host);
 template <typename T, int DIM>
 void coarse_pre(hf_mesh* h, const Krylov<T>& K, const T* rin, const int* skip, cudaStream_t st);

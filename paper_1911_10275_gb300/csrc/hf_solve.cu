@@ -34,31 +34,6 @@ constexpr int RB = 256;  // threads of reduction kernels
 
 template <typename T> __device__ __forceinline__ T ld(const T* p) { return __ldg(p); }
 
-// 16-byte vectors for the Krylov kernels: 4 floats or 2 doubles per load
-template <typename T> struct Vec;
-template <> struct Vec<float> {
-  using type = float4;
-  static constexpr int n = 4;
-  __device__ static float dot(const float4& a, const float4& b) { return a.x * b.x + a.y * b.y + a.z * b.z + a.w * b.w; }
-  __device__ static void axpy(float4& y, float a, const float4& x) {
-    y.x -= a * x.x; y.y -= a * x.y; y.z -= a * x.z; y.w -= a * x.w;
-  }
-  __device__ static void fma(float4& y, float a, const float4& x) {
-    y.x += a * x.x; y.y += a * x.y; y.z += a * x.z; y.w += a * x.w;
-  }
-  __device__ static float4 scale(const float4& x, float a) { return make_float4(a * x.x, a * x.y, a * x.z, a * x.w); }
-  __device__ static float4 zero() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-};
-template <> struct Vec<double> {
-  using type = double2;
-  static constexpr int n = 2;
-  __device__ static double dot(const double2& a, const double2& b) { return a.x * b.x + a.y * b.y; }
-  __device__ static void axpy(double2& y, double a, const double2& x) { y.x -= a * x.x; y.y -= a * x.y; }
-  __device__ static void fma(double2& y, double a, const double2& x) { y.x += a * x.x; y.y += a * x.y; }
-  __device__ static double2 scale(const double2& x, double a) { return make_double2(a * x.x, a * x.y); }
-  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
-};
-
 // ------------------------------------------------------------------ SpMV
 // MODE 0: y = J x.  MODE 1 (T = double): y = R(x), the residual.
 template <typename T, int DIM, int MODE>
@@ -1501,22 +1476,37 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
       }
     }
   } else {
-    T uu = (T)0, uw = (T)0;
+    // consumers: 16-byte vector loads from shared memory, one accumulator per
+    // vector component; a segment shorter than TR (the slice's last tile)
+    // takes its whole vectors first, then its last rows one by one
+    using VT = typename Vec<T>::type;
+    constexpr int VN = Vec<T>::n, VPT = TR / (VN * NC);
+    static_assert(TR % (VN * NC) == 0, "a segment splits evenly into the consumers' vectors");
     if (nt > 0) mbar_wait(uwbar, 0u, err, polls);
-    for (long long l = threadIdx.x; l < nr; l += NC) {
-      const T uv = us[l], wv = wsl[l];
-      uu += uv * uv;
-      uw += uv * wv;
-    }
     {
-      const double a = warp_sum((double)uu), b = warp_sum((double)uw);
+      VT uu = Vec<T>::zero(), uw = Vec<T>::zero();
+      const VT* u4 = reinterpret_cast<const VT*>(us);
+      const VT* w4 = reinterpret_cast<const VT*>(wsl);
+      const long long nv = nr / VN;
+      for (long long i = threadIdx.x; i < nv; i += NC) {
+        const VT a = u4[i], b = w4[i];
+        Vec<T>::madd(uu, a, a);
+        Vec<T>::madd(uw, a, b);
+      }
+      T su = Vec<T>::hsum(uu), sw = Vec<T>::hsum(uw);
+      for (long long l = nv * VN + threadIdx.x; l < nr; l += NC) {
+        su += us[l] * us[l];
+        sw += us[l] * wsl[l];
+      }
+      const double a = warp_sum((double)su), b = warp_sum((double)sw);
       if (lane == 0) {
         wsum[warp * DC_LD + 2 * j] = a;
         wsum[warp * DC_LD + 2 * j + 1] = b;
       }
     }
     for (int c = 0; c < j; ++c) {
-      T au = (T)0, aw = (T)0;
+      VT au = Vec<T>::zero(), aw = Vec<T>::zero();
+      T tu = (T)0, tw = (T)0;
       for (int t = 0; t < nt; ++t) {
         const long long k = (long long)c * nt + t;
         const int q = (int)(k % S);
@@ -1524,16 +1514,34 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
         const T* seg = ring + (size_t)q * TR;
         const T* ut = us + (size_t)t * TR;
         const T* wt = wsl + (size_t)t * TR;
+        const VT* seg4 = reinterpret_cast<const VT*>(seg);
+        const VT* ut4 = reinterpret_cast<const VT*>(ut);
+        const VT* wt4 = reinterpret_cast<const VT*>(wt);
         const int rows = (int)(nr - (long long)t * TR < TR ? nr - (long long)t * TR : TR);
-        for (int l = threadIdx.x; l < rows; l += NC) {
-          const T qv = seg[l];
-          au += qv * ut[l];
-          aw += qv * wt[l];
+        if (rows == TR) {
+#pragma unroll
+          for (int e = 0; e < VPT; ++e) {
+            const int i = threadIdx.x + e * NC;
+            const VT qv = seg4[i];
+            Vec<T>::madd(au, qv, ut4[i]);
+            Vec<T>::madd(aw, qv, wt4[i]);
+          }
+        } else {
+          const int nv = rows / VN;
+          for (int i = threadIdx.x; i < nv; i += NC) {
+            const VT qv = seg4[i];
+            Vec<T>::madd(au, qv, ut4[i]);
+            Vec<T>::madd(aw, qv, wt4[i]);
+          }
+          for (int l = nv * VN + threadIdx.x; l < rows; l += NC) {
+            tu += seg[l] * ut[l];
+            tw += seg[l] * wt[l];
+          }
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[q]);
       }
-      const double a = warp_sum((double)au), b = warp_sum((double)aw);
+      const double a = warp_sum((double)(Vec<T>::hsum(au) + tu)), b = warp_sum((double)(Vec<T>::hsum(aw) + tw));
       if (lane == 0) {
         wsum[warp * DC_LD + c] = a;
         wsum[warp * DC_LD + j + c] = b;
@@ -1561,7 +1569,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
                                                                long long n, const double* part, GmresState* gs,
                                                                int mrest, long long rb, int polls, int* err) {
   if (gs->done) return;
-  constexpr int S = DcTma<T>::S, TR = DcTma<T>::TR, NC = DCT_CONS * 32, RPT = TR / NC;
+  constexpr int S = DcTma<T>::S, TR = DcTma<T>::TR, NC = DCT_CONS * 32;
   __shared__ double red[DC_LD];
   __shared__ T coef[2 * GM_MAX];
   __shared__ double hc[GM_LD + 1], cvec[GM_LD];
@@ -1684,25 +1692,34 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
     }
     return;
   }
+  // each consumer thread owns VPT vectors of every tile; it loads the whole
+  // vector even past the slice's last row (the ring slot is TR long, the
+  // values there are never stored)
+  using VT = typename Vec<T>::type;
+  constexpr int VN = Vec<T>::n, VPT = TR / (VN * NC);
+  static_assert(TR % (VN * NC) == 0, "a segment splits evenly into the consumers' vectors");
   const T ir = (T)inv_r, dd = (T)d;
   for (int t = 0; t < nt; ++t) {
     const int rows = (int)(nr - (long long)t * TR < TR ? nr - (long long)t * TR : TR);
-    T su[RPT], sw[RPT];
+    VT su[VPT], sw[VPT];
     for (int m = 0; m < per; ++m) {
       const long long k = (long long)t * per + m;
       const int q = (int)(k % S);
       mbar_wait(&full[q], (unsigned)((k / S) & 1), err, polls);
-      const T* seg = ring + (size_t)q * TR;
-      const T cu = m >= 2 ? coef[m - 2] : (T)0, cw = m >= 2 ? coef[GM_MAX + m - 2] : (T)0;
+      const VT* seg = reinterpret_cast<const VT*>(ring + (size_t)q * TR);
+      if (m == 0) {
 #pragma unroll
-      for (int e = 0; e < RPT; ++e) {
-        const int l = threadIdx.x + e * NC;
-        const T v = l < rows ? seg[l] : (T)0;
-        if (m == 0) su[e] = v;
-        else if (m == 1) sw[e] = v;
-        else {
-          su[e] -= cu * v;
-          sw[e] -= cw * v;
+        for (int e = 0; e < VPT; ++e) su[e] = seg[threadIdx.x + e * NC];
+      } else if (m == 1) {
+#pragma unroll
+        for (int e = 0; e < VPT; ++e) sw[e] = seg[threadIdx.x + e * NC];
+      } else {
+        const T cu = coef[m - 2], cw = coef[GM_MAX + m - 2];
+#pragma unroll
+        for (int e = 0; e < VPT; ++e) {
+          const VT v = seg[threadIdx.x + e * NC];
+          Vec<T>::axpy(su[e], cu, v);
+          Vec<T>::axpy(sw[e], cw, v);
         }
       }
       __syncwarp();
@@ -1710,12 +1727,22 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
     }
     const long long a = r0 + (long long)t * TR;
 #pragma unroll
-    for (int e = 0; e < RPT; ++e) {
-      const int l = threadIdx.x + e * NC;
-      if (l < rows) {
-        const T vj = su[e] * ir;
-        if (j > 0) u[a + l] = vj;
-        un[a + l] = (sw[e] - dd * vj) * ir;
+    for (int e = 0; e < VPT; ++e) {
+      const int l = (threadIdx.x + e * NC) * VN;
+      const VT vj = Vec<T>::scale(su[e], ir);
+      VT wn = sw[e];
+      Vec<T>::axpy(wn, dd, vj);
+      wn = Vec<T>::scale(wn, ir);
+      if (l + VN <= rows) {
+        if (j > 0) *reinterpret_cast<VT*>(u + a + l) = vj;
+        *reinterpret_cast<VT*>(un + a + l) = wn;
+      } else if (l < rows) {
+        const T* pv = reinterpret_cast<const T*>(&vj);
+        const T* pw = reinterpret_cast<const T*>(&wn);
+        for (int c = 0; c < VN && l + c < rows; ++c) {
+          if (j > 0) u[a + l + c] = pv[c];
+          un[a + l + c] = pw[c];
+        }
       }
     }
   }

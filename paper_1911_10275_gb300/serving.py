@@ -55,8 +55,11 @@ def latency_summary(records):
     """p50 / p99 / max latency in ms over successful requests, throughput in
     requests/s over the span from the first submit to the last completion."""
     ok = [r for r in records if r["status"] == 0]
+    failures = [{"name": r.get("name"), "status": int(r["status"]), "newton_iters": int(r["newton_iters"]),
+                 "cutbacks": int(r["cutbacks"]), "steps_done": int(r.get("steps_done", -1))}
+                for r in records if r["status"] != 0]
     if not ok:
-        return {"completed": 0, "failed": len(records)}
+        return {"completed": 0, "failed": len(records), "failures": failures}
     lat = np.array([r["latency"] for r in ok]) * 1000.0
     span = max(r["t_done"] for r in records) - min(r["t_submit"] for r in records)
     return {"completed": len(ok), "failed": len(records) - len(ok),
@@ -65,4 +68,4 @@ def latency_summary(records):
             "throughput_req_s": len(ok) / span if span > 0 else None,
             "newton_iters": int(sum(r["newton_iters"] for r in ok)),
             "gmres_iters": int(sum(r["gmres_iters"] for r in ok)),
-            "cutbacks": int(sum(r["cutbacks"] for r in ok))}
+            "cutbacks": int(sum(r["cutbacks"] for r in ok)), "failures": failures}

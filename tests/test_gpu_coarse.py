@@ -62,10 +62,11 @@ def _gpu_basis(mesh, agg, geo):
 CASES = [lambda: kgd_2d(n=10, length=20.0), lambda: penny_3d(n=4, crackable="plane")]
 
 
-@pytest.mark.parametrize("make", CASES)
-def test_coarse_operator_is_phi_t_j_phi(make):
+@pytest.mark.parametrize("make,coarse_max", [(CASES[0], 64), (CASES[1], 64), (CASES[1], 260)])
+def test_coarse_operator_is_phi_t_j_phi(make, coarse_max):
     """A0 as built on the GPU equals Phi^T J Phi in the library's basis, and
-    the stored inverse inverts it."""
+    the stored inverse inverts it (258 coarse unknowns at 260: several pivot
+    blocks of the blocked inversion, a ragged last block and several tiles)."""
     wl = make()
     m = wl.mesh
     U, P, al, be = wl.seed()
@@ -74,13 +75,15 @@ def test_coarse_operator_is_phi_t_j_phi(make):
     o.set_state(*state)
     _, J = o.assemble()
     Juu = J.tocsr()[:o.Nu, :o.Nu]
-    g = gpu_for(wl, precision="fp64", jacobi_block=8, coarse=1, coarse_max=64)
+    g = gpu_for(wl, precision="fp64", jacobi_block=8, coarse=1, coarse_max=coarse_max)
     g.hf_set_state(*state)
     agg = g.hf_get_aggregates()
     A0g, invg, geo = g.hf_get_coarse_operator()
     g.close()
     Phi = _gpu_basis(m, agg, geo)
     A0 = Phi.T @ (Juu @ Phi)
+    if coarse_max > 64:
+        assert A0.shape[0] > 2 * 64 and A0.shape[0] % 32 != 0, A0.shape
     assert np.abs(A0g - A0).max() <= 1e-12 * np.abs(A0).max()
     assert np.abs(invg @ A0 - np.eye(A0.shape[0])).max() <= 1e-9
 
