@@ -589,7 +589,7 @@ def _solver_for_requests(args, tuner=None):
     return lambda wl: {**tuner.solver_for(wl, args.precision), "max_iters": args.request_max_iters}
 
 
-REQUEST_STEP = {"newton_max": 8, "criterion_rounds": 4, "max_cutbacks": 4}
+REQUEST_STEP = {"newton_max": 8, "criterion_rounds": 4, "max_cutbacks": 10}
 
 
 def serving_run(args, count, rate, slots, seed=191110275, warm=True):

@@ -293,6 +293,12 @@ typedef struct {
   int criterion_rounds;  /* criterion / Newton-again rounds per sub-step (default 4) */
   int max_cutbacks;      /* consecutive failed attempts (each halving the sub-step) before the call
                            gives up (default 10); at most 256 attempts in all */
+  int max_new_facets;    /* an attempt whose fracture criterion switches more than this many facets
+                           in one round fails like a non-converged one (undone, sub-step halved):
+                           the criterion is checked on the converged state of a sub-step at fixed
+                           crack, and a sub-step that injects far more fluid than the crack holds
+                           overshoots the pressure and switches a whole region at once.  0 (the
+                           default): no limit */
 } hf_step_opts;
 
 typedef struct {
@@ -316,7 +322,8 @@ void hf_default_step_opts(hf_step_opts* o);
  * iterations, whose linear solve misses its tolerance by more than a factor
  * of 10 (the FP64 solve ends early when five restarts in a row each reduce
  * the residual by less than 1%), or whose state turns
- * non-finite is undone from a device copy of the start-of-step state and
+ * non-finite, or whose criterion switches more than max_new_facets facets in
+ * one round, is undone from a device copy of the start-of-step state and
  * retried with half the sub-step; after a success the sub-step grows by 1.5
  * up to dt, until t + dt is reached.  dt itself is left unchanged.  Errors:
  * HF_ERR_NOT_CONVERGED after max_cutbacks consecutive failures or 256

@@ -50,7 +50,8 @@ class hf_newton_report(C.Structure):
 
 
 class hf_step_opts(C.Structure):
-    _fields_ = [("newton_max", C.c_int), ("criterion_rounds", C.c_int), ("max_cutbacks", C.c_int)]
+    _fields_ = [("newton_max", C.c_int), ("criterion_rounds", C.c_int), ("max_cutbacks", C.c_int),
+                ("max_new_facets", C.c_int)]
 
 
 class hf_step_report(C.Structure):

@@ -1294,6 +1294,7 @@ void hf_default_step_opts(hf_step_opts* o) {
   o->newton_max = 8;
   o->criterion_rounds = 4;
   o->max_cutbacks = 10;
+  o->max_new_facets = 0;
 }
 
 hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* rep) {
@@ -1302,7 +1303,7 @@ hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* 
   hf_step_opts o;
   hf_default_step_opts(&o);
   if (opts) o = *opts;
-  if (o.newton_max < 1 || o.criterion_rounds < 1 || o.max_cutbacks < 0)
+  if (o.newton_max < 1 || o.criterion_rounds < 1 || o.max_cutbacks < 0 || o.max_new_facets < 0)
     return set_error(h, HF_ERR_INVALID_ARG, "step options out of range");
   hf_step_report r{};
   const double dt0 = h->dt, target = h->t + dt0;
@@ -1343,6 +1344,8 @@ hf_status hf_advance_step(hf_mesh* h, const hf_step_opts* opts, hf_step_report* 
           return s;
         }
         r.new_alpha += na;
+        // a whole region switched at once: the sub-step overshot
+        if (o.max_new_facets > 0 && na > o.max_new_facets) break;
         if (na == 0 || ++rounds >= o.criterion_rounds) {
           ok = true;
           break;

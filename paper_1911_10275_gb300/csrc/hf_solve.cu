@@ -1098,7 +1098,13 @@ __global__ void __launch_bounds__(GS_T) k_gs_fin(const T* __restrict__ V_in, T* 
 // The convergence test of column j-1 runs at step j; at the end of a cycle a
 // last reduction finalises column m-1.
 constexpr int DC_LD = 2 * GM_MAX + 2;  // row length of the reduction table
-constexpr int DC_SLAB = 12288;                          // doubles staged at a time by dc_reduce
+// The reduction table of the delayed CGS2 step holds values of the Krylov
+// type T: the FP32 path adds its partial sums in FP32 all the way to the
+// per-CTA rows and across them (one conversion to FP64 per column at the
+// end).  Its products already carry FP32 rounding, and FP64 arithmetic runs
+// at a small fraction of the FP32 rate on this GPU: per-column FP64 shuffle
+// reductions took longer than streaming the column itself.
+constexpr int DC_SLAB = 12288;                          // table values staged at a time by dc_reduce
 constexpr size_t DC_SMEM = DC_SLAB * sizeof(double);   // 96 KiB of dynamic shared memory (opt-in)
 
 // block partials of [Q^T u, Q^T w, u.u, u.w] (w != null) or [Q^T u, u.u]
@@ -1109,13 +1115,13 @@ __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long l
   if (gs->done) return;
   using VT = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n, NW = GS_T / 32, CH = sizeof(T) == 4 ? 16 : 8;
-  __shared__ double ws[NW][2 * CH + 2];
+  __shared__ T ws[NW][2 * CH + 2];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long stride = (long long)gridDim.x * blockDim.x, tid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   const long long nv = n / VN;
   const T* u = V + (long long)j * ldv;
   const bool hw = w != nullptr;
-  double* row = part + (long long)blockIdx.x * DC_LD;
+  T* row = reinterpret_cast<T*>(part) + (long long)blockIdx.x * DC_LD;
   const int nchunks = j > 0 ? (j + CH - 1) / CH : 1;
   for (int ch = 0; ch < nchunks; ++ch) {
     const int q0 = ch * CH, nq = max(0, min(CH, j - q0));
@@ -1178,11 +1184,11 @@ __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long l
       sw = aw[0];
     }
     if (lane < CH) {
-      ws[warp][lane] = (double)su;
-      ws[warp][CH + lane] = (double)sw;
+      ws[warp][lane] = su;
+      ws[warp][CH + lane] = sw;
     }
     if (first) {
-      const double a = warp_sum((double)uu), b = warp_sum((double)uw);
+      const T a = warp_sum(uu), b = warp_sum(uw);
       if (lane == 0) {
         ws[warp][2 * CH] = a;
         ws[warp][2 * CH + 1] = b;
@@ -1191,7 +1197,7 @@ __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long l
     __syncthreads();
     const int t = threadIdx.x;
     if (t < 2 * CH + 2) {
-      double s = 0.0;
+      T s = (T)0;
       for (int k = 0; k < NW; ++k) s += ws[k][t];
       if (t < CH) {
         if (t < nq) row[q0 + t] = s;
@@ -1211,25 +1217,28 @@ __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long l
 // DC_SLAB values at a time, four independent loads per thread and pass),
 // then G threads per column add interleaved rows and their G partial sums
 // meet in a fixed order: the same order, hence the same result, in every CTA
-__device__ void dc_reduce(const double* part, int nb, int nvc, double* out) {
-  extern __shared__ double stage[];
-  __shared__ double gpart[GS_T];
+template <typename RT>
+__device__ void dc_reduce(const double* part_raw, int nb, int nvc, double* out) {
+  extern __shared__ __align__(16) unsigned char stage_raw[];
+  RT* stage = reinterpret_cast<RT*>(stage_raw);
+  const RT* part = reinterpret_cast<const RT*>(part_raw);
+  __shared__ RT gpart[GS_T];
   const int rows_per = max(1, DC_SLAB / max(nvc, 1));
   const int nth = min((int)blockDim.x, GS_T);  // threads past GS_T only join the barriers
   const int G = max(1, min(8, nth / max(nvc, 1)));
   const int c = threadIdx.x % max(nvc, 1), g = (int)threadIdx.x < nth ? threadIdx.x / max(nvc, 1) : G;
-  double acc = 0.0;
+  RT acc = (RT)0;
   for (int r0 = 0; r0 < nb; r0 += rows_per) {
     const int nr = min(rows_per, nb - r0);
     const int tot = nr * nvc;
     __syncthreads();
     for (int t = threadIdx.x; t < tot; t += 4 * nth) {
       if ((int)threadIdx.x >= nth) break;
-      double v[4];
+      RT v[4];
 #pragma unroll
       for (int k = 0; k < 4; ++k) {
         const int tt = t + k * nth;
-        v[k] = 0.0;
+        v[k] = (RT)0;
         if (tt < tot) {
           const int rr = tt / nvc;
           v[k] = __ldcg(part + (long long)(r0 + rr) * DC_LD + (tt - rr * nvc));
@@ -1246,9 +1255,9 @@ __device__ void dc_reduce(const double* part, int nb, int nvc, double* out) {
   if (g < G) gpart[g * nvc + c] = acc;
   __syncthreads();
   for (int cc = threadIdx.x; cc < nvc; cc += nth) {
-    double t = 0.0;
+    RT t = (RT)0;
     for (int k = 0; k < G; ++k) t += gpart[k * nvc + cc];
-    out[cc] = t;
+    out[cc] = (double)t;
   }
   __syncthreads();
 }
@@ -1296,7 +1305,7 @@ __global__ void __launch_bounds__(GS_T) k_dc_upd(T* V, long long ldv, int j, con
   __shared__ double hc[GM_LD + 1], cvec[GM_LD];
   const int nb = gridDim.x;
   const int nvc = 2 * j + 2;
-  dc_reduce(part, nb, nvc, red);
+  dc_reduce<T>(part, nb, nvc, red);
   const double uu = red[2 * j], uw = red[2 * j + 1];
   double ab = 0.0, aa = 0.0;
   for (int k = 0; k < j; ++k) {
@@ -1436,7 +1445,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
   T* us = reinterpret_cast<T*>(dsm);
   T* wsl = us + rb;
   T* ring = wsl + rb;
-  double* wsum = reinterpret_cast<double*>(ring + (size_t)S * TR);  // [DCT_CONS][DC_LD]
+  T* wsum = ring + (size_t)S * TR;  // [DCT_CONS][DC_LD]
   unsigned long long* full = reinterpret_cast<unsigned long long*>(wsum + DCT_CONS * DC_LD);
   unsigned long long* empty = full + S;
   unsigned long long* uwbar = empty + S;
@@ -1498,7 +1507,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
         su += us[l] * us[l];
         sw += us[l] * wsl[l];
       }
-      const double a = warp_sum((double)su), b = warp_sum((double)sw);
+      const T a = warp_sum(su), b = warp_sum(sw);
       if (lane == 0) {
         wsum[warp * DC_LD + 2 * j] = a;
         wsum[warp * DC_LD + 2 * j + 1] = b;
@@ -1541,7 +1550,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
         __syncwarp();
         if (lane == 0) mbar_arrive(&empty[q]);
       }
-      const double a = warp_sum((double)(Vec<T>::hsum(au) + tu)), b = warp_sum((double)(Vec<T>::hsum(aw) + tw));
+      const T a = warp_sum(Vec<T>::hsum(au) + tu), b = warp_sum(Vec<T>::hsum(aw) + tw);
       if (lane == 0) {
         wsum[warp * DC_LD + c] = a;
         wsum[warp * DC_LD + j + c] = b;
@@ -1550,9 +1559,9 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
     if (warp == 0 && lane == 0) dct_drain(full, S, (long long)j * nt, err, polls);
   }
   __syncthreads();
-  double* row = part + (long long)blockIdx.x * DC_LD;
+  T* row = reinterpret_cast<T*>(part) + (long long)blockIdx.x * DC_LD;
   for (int c = threadIdx.x; c < 2 * j + 2; c += blockDim.x) {
-    double sacc = 0.0;
+    T sacc = (T)0;
     for (int k = 0; k < DCT_CONS; ++k) sacc += wsum[k * DC_LD + c];
     row[c] = sacc;
   }
@@ -1575,7 +1584,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
   __shared__ double hc[GM_LD + 1], cvec[GM_LD];
   __shared__ __align__(8) unsigned long long full[S], empty[S];
   const int nb = gridDim.x;
-  dc_reduce(part, nb, 2 * j + 2, red);
+  dc_reduce<T>(part, nb, 2 * j + 2, red);
   const double uu = red[2 * j], uw = red[2 * j + 1];
   double ab = 0.0, aa = 0.0;
   for (int k = 0; k < j; ++k) {
@@ -1751,11 +1760,12 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
 
 // end of a cycle that ran all mrest steps: finalise column mrest - 1 from
 // the reduction of [Q^T u_m, u_m.u_m]
+template <typename T>
 __global__ void __launch_bounds__(GS_T) k_dc_close(const double* part, int nb, int m, GmresState* gs) {
   if (gs->done) return;
   __shared__ double red[DC_LD];
   __shared__ double hc[GM_LD + 1];
-  dc_reduce(part, nb, m + 1, red);
+  dc_reduce<T>(part, nb, m + 1, red);
   double aa = 0.0;
   for (int k = 0; k < m; ++k) aa += red[k] * red[k];
   const double r2 = red[m] - aa;
@@ -2107,7 +2117,7 @@ template <typename T> static void dc_configure() {
   static std::once_flag once;
   std::call_once(once, [] {
     cudaFuncSetAttribute(k_dc_upd<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DC_SMEM);
-    cudaFuncSetAttribute(k_dc_close, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DC_SMEM);
+    cudaFuncSetAttribute(k_dc_close<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)DC_SMEM);
     cudaFuncAttributes fa{};
     if (cudaFuncGetAttributes(&fa, k_dc_dot_tma<T>) == cudaSuccess)
       cudaFuncSetAttribute(k_dc_dot_tma<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -2124,7 +2134,7 @@ template <typename T> static void dc_configure() {
 // or 0 when it does not fit beside the kernel's static shared memory
 template <typename T> static size_t dct_dot_smem(long long rb) {
   const size_t b = (size_t)2 * rb * sizeof(T) + (size_t)DcTma<T>::S * DcTma<T>::TR * sizeof(T) +
-                   (size_t)DCT_CONS * DC_LD * sizeof(double) + (size_t)(2 * DcTma<T>::S + 1) * 8;
+                   (size_t)DCT_CONS * DC_LD * sizeof(T) + (size_t)(2 * DcTma<T>::S + 1) * 8;
   cudaFuncAttributes fa{};
   if (cudaFuncGetAttributes(&fa, k_dc_dot_tma<T>) != cudaSuccess) {
     cudaGetLastError();
@@ -2350,7 +2360,7 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
     const T* um = K.V + (long long)mrest * K.ldv;
     (void)um;
     { note_launch(); k_dc_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, mrest, nullptr, N, h->d_partial, gs); }
-    { note_launch(); k_dc_close<<<1, GS_T, DC_SMEM, h->stream>>>(h->d_partial, nb, mrest, gs); }
+    { note_launch(); k_dc_close<T><<<1, GS_T, DC_SMEM, h->stream>>>(h->d_partial, nb, mrest, gs); }
   }
   {
     const size_t sm = ((size_t)mrest * GM_LD + GM_LD) * sizeof(double);

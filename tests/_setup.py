@@ -51,7 +51,7 @@ def rel_err(a, b):
     return np.abs(a - b).max() / (scale if scale > 0 else 1.0)
 
 
-def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=None, log=None):
+def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=None, log=None, max_new_facets=0):
     """One time step of Sec. 3 on the oracle, with the driver rules of
     hf_advance_step: Newton until converged, the criterion, Newton again if it
     switched facets (at most rounds_max rounds), end of step; an attempt that
@@ -60,7 +60,9 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
     each accepted sub-step until t + dt is reached; at most max_cutbacks
     failures in a row, 256 attempts in all.  Past newton_max an attempt goes
     on while the increments at least halve every iteration (at most
-    4 newton_max iterations).  ``newton()`` replaces ``o.newton_step()``
+    4 newton_max iterations); with max_new_facets > 0 an attempt whose
+    criterion switches more facets than that in one round fails too.
+    ``newton()`` replaces ``o.newton_step()``
     (the same iteration with pooled assembly, say).  With ``log`` a list, one
     record per attempt is appended: its sub-step, the Newton iterations of
     each Newton round (a round ends with the fracture criterion), the facets
@@ -92,6 +94,9 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
                 rounds += 1
                 rec["rounds"].append(it)
                 rec["switched"].append(int(n_new))
+                if max_new_facets > 0 and n_new > max_new_facets:
+                    it = None      # this round is recorded already
+                    break
                 if n_new == 0 or rounds >= rounds_max:
                     ok = True
                     break
@@ -102,7 +107,7 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
                 break
             prev = inc
         attempts += 1
-        if not ok:
+        if not ok and it is not None:
             rec["rounds"].append(it)
         rec["accepted"] = ok
         if log is not None:

@@ -15,10 +15,20 @@ same sub-step, the same number of Newton iterations per round, the fracture
 criterion after each round (it must switch the same number of facets), then
 the end of the step or the undo.  Per step the cohesive and fluid facets must
 be the same, and U on a fixed sample, every non-zero pressure and the
-openings at the face nodes of every cohesive or fluid facet within 1e-9 of
+openings at the face nodes of every cohesive or fluid facet within 1e-8 of
 the oracle's (each over the infinity norm of the oracle's field).
-hf_advance_step's own decisions are checked against the oracle's driver in
-tests/test_gpu_runtime.py."""
+
+The trajectory tolerance follows from the Newton tolerance, not from the
+per-iteration parity: an attempt stops when both relative increments are at
+most 1e-10, and with the cut-off active Newton converges linearly (rate
+rho up to about 0.9 in these steps), so each side's end-of-step state lies
+within about 1e-10 / (1 - rho) = 1e-9 of the discrete solution; the
+difference of the two sides carries into the next step, so after k steps
+it is bounded by about 2k x 1e-9.  For ten steps 1e-8 is asserted (the
+largest seen is 2.5e-9, at step 7).  The per-iteration parity, 1e-10 in
+FP64 from the same state, is checked at this size by
+test_c1_newton_step_matches_oracle.  hf_advance_step's own decisions are
+checked against the oracle's driver in tests/test_gpu_runtime.py."""
 import json
 import os
 
@@ -26,6 +36,7 @@ import numpy as np
 import pytest
 
 from hf_inputs import c1_kgd_toughness
+from _setup import oracle_for, gpu_for, with_extra_cohesive, rel_err
 
 pytestmark = pytest.mark.gpu
 
@@ -75,6 +86,29 @@ def test_c1_ten_time_steps_match_oracle():
         ep = np.abs(P[pi] - np.asarray(rec["P"])).max() / rec["P_inf"]
         wf = np.asarray(rec["w_faces"], dtype=np.int64)
         ew = np.abs(W[wf] - np.asarray(rec["w"])).max() / rec["w_inf"]
-        assert max(eu, ep, ew) <= 1e-9, (rec["k"], eu, ep, ew)
+        assert max(eu, ep, ew) <= 1e-8, (rec["k"], eu, ep, ew)
     set_dt(wl.dt)
     g.close()
+
+
+@pytest.mark.parametrize("extra", [0, 2])
+def test_c1_newton_step_matches_oracle(extra):
+    """One FP64 Newton iteration of the c1 mesh (46,553 unknowns) from the
+    same state on both sides, the seed alone or with two more cohesive
+    facets in the softening branch: U and P within 1e-10 of the oracle's
+    step (GMRES to 1e-13, the oracle's direct solve refined)."""
+    wl = c1_kgd_toughness()
+    state = wl.seed()
+    if extra:
+        state, _ = with_extra_cohesive(wl, state, count=extra)
+    o = oracle_for(wl, cutoff=True)
+    o.set_state(*state)
+    g = gpu_for(wl, cutoff=True, precision="fp64", rtol=1e-13, max_iters=20000, jacobi_block=16)
+    g.hf_set_state(*state)
+    rep = g.hf_newton_step()
+    o.newton_step()
+    Ug, Pg = g.hf_get_state()[:2]
+    g.close()
+    assert rep["lin_converged"], rep
+    assert rel_err(Ug, o.U) <= 1e-10
+    assert rel_err(Pg, o.P) <= 1e-10
