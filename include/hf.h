@@ -96,7 +96,10 @@ typedef struct {
   int restart;          /* GMRES restart length m (1..96; default 60) */
   int max_iters;        /* cap on GMRES iterations per Newton step (all cycles) */
   double rtol;          /* GMRES: ||J d + R|| <= rtol ||R|| */
-  double inner_rtol;    /* mixed: reduction asked of each FP32 inner solve */
+  double inner_rtol;    /* mixed: reduction asked of each FP32 inner solve (default 1e-4); after
+                           two sweeps in a row that do not halve the FP64 residual the solve
+                           goes on in FP64, so a value >= 1 (no reduction asked) makes every
+                           mixed solve finish in FP64 */
   int jacobi_block;     /* elements per block-Jacobi subdomain (>= 1) */
   int fluid_scaling;    /* 1: scale pressure rows by c^n (remark in Sec. 3) */
   double newton_tol;    /* relative-increment tolerance of hf_newton_step */

@@ -540,8 +540,11 @@ __device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned b
                : "memory");
 }
 // bounded wait on an mbarrier phase; after `polls` unsuccessful polls raise
-// the error flag and go on
-__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned phase, int* err, int polls) {
+// the error flag (the first site to give up: 1 ILU(0) apply, 2-4 the delayed
+// CGS2 dot kernel's producer, u/w and consumer waits, 5-6 the update
+// kernel's producer and consumer waits, 7 the drain, 8 the self-test) and go on
+__device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned phase, int* err, int polls,
+                                          int site = 1) {
   for (int it = 0; it < polls; ++it) {
     unsigned ok;
     asm volatile(
@@ -551,7 +554,7 @@ __device__ __forceinline__ void mbar_wait(unsigned long long* bar, unsigned phas
         : "memory");
     if (ok) return;
   }
-  atomicExch(err, 1);
+  atomicCAS(err, 0, site);  // the first wait that gave up names its site
 }
 
 // z = M^-1 rin on the displacement unknowns.  One warp per subdomain, no
@@ -747,6 +750,18 @@ __global__ void k_prec_p(DevMesh m, const T* __restrict__ rin, const double* sca
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
   if (lane == 0) z[m.nu + g] = (T)(((double)r - m.scal[0] * acc) * (double)sinv[g]);
+}
+
+// the Arnoldi cycle's done flag, read once per CTA: block 0 of the update
+// kernels sets it in the same launch in which the other CTAs read it, and a
+// CTA that starts late (other streams' kernels holding the SMs) must not let
+// its producer warp and its consumer warps see different values, or the
+// consumers wait for copies that are never issued
+__device__ __forceinline__ bool cta_done(const GmresState* gs) {
+  __shared__ int d;
+  if (threadIdx.x == 0) d = *reinterpret_cast<const volatile int*>(&gs->done);
+  __syncthreads();
+  return d != 0;
 }
 
 // ------------------------------------------------------------------ reductions
@@ -946,7 +961,7 @@ template <typename T>
 __global__ void __launch_bounds__(GS_T) k_gs_dot(const T* __restrict__ V, long long ldv, int j,
                                                  const T* __restrict__ w, long long n, double* part,
                                                  const GmresState* gs, int wnorm) {
-  if (gs->done) return;
+  if (cta_done(gs)) return;
   gs_partial_dots<T>(V, ldv, j + 1, w, n, part, wnorm != 0);
 }
 
@@ -957,7 +972,7 @@ template <typename T>
 __global__ void __launch_bounds__(GS_T) k_gs_sub(const T* __restrict__ V, long long ldv, int j, T* w, long long n,
                                                  const double* part, double* part2, GmresState* gs, int first,
                                                  int wnorm, const int* skipflag) {
-  if (gs->done || (skipflag && *skipflag)) return;
+  if (cta_done(gs) || (skipflag && *skipflag)) return;
   __shared__ double hs[GM_LD];
   __shared__ T ht[GM_MAX];
   const int ncols = j + 1;
@@ -1011,7 +1026,7 @@ __global__ void __launch_bounds__(GS_T) k_gs_fin(const T* __restrict__ V_in, T* 
                                                  const T* __restrict__ w, long long n, const double* part2,
                                                  double* part, GmresState* gs, int mrest, int mode, double eta,
                                                  const int* skipflag) {
-  if (gs->done || (skipflag && *skipflag)) return;
+  if (cta_done(gs) || (skipflag && *skipflag)) return;
   const int nb = gridDim.x;
   const double nrm2 = gs_reduce_vector(part2, nb);
   const double nrm = sqrt(nrm2);
@@ -1107,12 +1122,31 @@ constexpr int DC_LD = 2 * GM_MAX + 2;  // row length of the reduction table
 constexpr int DC_SLAB = 12288;                          // table values staged at a time by dc_reduce
 constexpr size_t DC_SMEM = DC_SLAB * sizeof(double);   // 96 KiB of dynamic shared memory (opt-in)
 
+// running sum with its rounding error carried beside it (Knuth's TwoSum:
+// s + c equals the exact sum of the added values up to O(eps^2)), for the
+// FP32 reductions of the delayed CGS2 step; FP64 sums stay plain (their
+// rounding is far below the FP32 products', and FP64 adds are scarce)
+template <typename T> struct CSum {
+  T s = (T)0, c = (T)0;
+  __device__ void add(T v) {
+    const T t = s + v, bp = t - s;
+    c += (s - (t - bp)) + (v - bp);
+    s = t;
+  }
+  __device__ double value() const { return (double)s + (double)c; }
+};
+template <> struct CSum<double> {
+  double s = 0.0;
+  __device__ void add(double v) { s += v; }
+  __device__ double value() const { return s; }
+};
+
 // block partials of [Q^T u, Q^T w, u.u, u.w] (w != null) or [Q^T u, u.u]
 template <typename T>
 __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long long ldv, int j,
                                                  const T* __restrict__ w, long long n, double* part,
                                                  const GmresState* gs) {
-  if (gs->done) return;
+  if (cta_done(gs)) return;
   using VT = typename Vec<T>::type;
   constexpr int VN = Vec<T>::n, NW = GS_T / 32, CH = sizeof(T) == 4 ? 16 : 8;
   __shared__ T ws[NW][2 * CH + 2];
@@ -1197,8 +1231,9 @@ __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long l
     __syncthreads();
     const int t = threadIdx.x;
     if (t < 2 * CH + 2) {
-      T s = (T)0;
-      for (int k = 0; k < NW; ++k) s += ws[k][t];
+      CSum<T> cs;
+      for (int k = 0; k < NW; ++k) cs.add(ws[k][t]);
+      const T s = (T)cs.value();
       if (t < CH) {
         if (t < nq) row[q0 + t] = s;
       } else if (t < 2 * CH) {
@@ -1222,12 +1257,12 @@ __device__ void dc_reduce(const double* part_raw, int nb, int nvc, double* out) 
   extern __shared__ __align__(16) unsigned char stage_raw[];
   RT* stage = reinterpret_cast<RT*>(stage_raw);
   const RT* part = reinterpret_cast<const RT*>(part_raw);
-  __shared__ RT gpart[GS_T];
+  __shared__ double gpart[GS_T];
   const int rows_per = max(1, DC_SLAB / max(nvc, 1));
   const int nth = min((int)blockDim.x, GS_T);  // threads past GS_T only join the barriers
   const int G = max(1, min(8, nth / max(nvc, 1)));
   const int c = threadIdx.x % max(nvc, 1), g = (int)threadIdx.x < nth ? threadIdx.x / max(nvc, 1) : G;
-  RT acc = (RT)0;
+  CSum<RT> acc;
   for (int r0 = 0; r0 < nb; r0 += rows_per) {
     const int nr = min(rows_per, nb - r0);
     const int tot = nr * nvc;
@@ -1250,14 +1285,40 @@ __device__ void dc_reduce(const double* part_raw, int nb, int nvc, double* out) 
     }
     __syncthreads();
     if (g < G)
-      for (int rr = g; rr < nr; rr += G) acc += stage[rr * nvc + c];
+      for (int rr = g; rr < nr; rr += G) acc.add(stage[rr * nvc + c]);
   }
-  if (g < G) gpart[g * nvc + c] = acc;
+  if (g < G) gpart[g * nvc + c] = acc.value();
   __syncthreads();
   for (int cc = threadIdx.x; cc < nvc; cc += nth) {
-    RT t = (RT)0;
+    double t = 0.0;
     for (int k = 0; k < G; ++k) t += gpart[k * nvc + cc];
-    out[cc] = (double)t;
+    out[cc] = t;
+  }
+  __syncthreads();
+}
+
+// r = sqrt(u.u - a.a), 1 / r and d = (u.w - a.b) / r of the delayed CGS2
+// step, from the reduced table: one warp adds the j products (lanes over k,
+// then a fixed butterfly), the block reads the three numbers from shared
+// memory.  Every CTA computes them in the same order, hence identically;
+// one warp instead of every thread, because FP64 arithmetic is scarce here.
+__device__ void dc_scalars(const double* red, int j, double* sc) {
+  if (threadIdx.x < 32) {
+    double ab = 0.0, aa = 0.0;
+    for (int k = threadIdx.x; k < j; k += 32) {
+      ab += red[k] * red[j + k];
+      aa += red[k] * red[k];
+    }
+    ab = warp_sum(ab);
+    aa = warp_sum(aa);
+    if (threadIdx.x == 0) {
+      const double r2 = red[2 * j] - aa;
+      const double r = j == 0 ? 1.0 : (r2 > 0.0 ? sqrt(r2) : 0.0);
+      const double inv_r = r > 0.0 ? 1.0 / r : 0.0;
+      sc[0] = r;
+      sc[1] = inv_r;
+      sc[2] = (red[2 * j + 1] - ab) * inv_r;
+    }
   }
   __syncthreads();
 }
@@ -1299,23 +1360,16 @@ __device__ void dc_givens_block(GmresState* gs, double* hc, int jc, int mrest) {
 template <typename T>
 __global__ void __launch_bounds__(GS_T) k_dc_upd(T* V, long long ldv, int j, const T* __restrict__ w, long long n,
                                                  const double* part, GmresState* gs, int mrest) {
-  if (gs->done) return;
+  if (cta_done(gs)) return;
   __shared__ double red[DC_LD];
   __shared__ T coef[2 * GM_MAX];
   __shared__ double hc[GM_LD + 1], cvec[GM_LD];
   const int nb = gridDim.x;
   const int nvc = 2 * j + 2;
   dc_reduce<T>(part, nb, nvc, red);
-  const double uu = red[2 * j], uw = red[2 * j + 1];
-  double ab = 0.0, aa = 0.0;
-  for (int k = 0; k < j; ++k) {
-    ab += red[k] * red[j + k];
-    aa += red[k] * red[k];
-  }
-  const double r2 = uu - aa;
-  const double r = j == 0 ? 1.0 : (r2 > 0.0 ? sqrt(r2) : 0.0);
-  const double inv_r = r > 0.0 ? 1.0 / r : 0.0;
-  const double d = (uw - ab) * inv_r;
+  __shared__ double sc[3];
+  dc_scalars(red, j, sc);
+  const double uw = red[2 * j + 1], r = sc[0], inv_r = sc[1], d = sc[2];
   if (blockIdx.x == 0) {
     // Hessenberg bookkeeping (no sweep in this block)
     if (j == 0) {
@@ -1423,7 +1477,7 @@ __device__ __forceinline__ void sync_gs() { asm volatile("bar.sync 1, %0;" ::"n"
 __device__ __forceinline__ void dct_drain(unsigned long long* full, int S, long long nseg, int* err, int polls) {
   for (int q = 0; q < S && q < nseg; ++q) {
     const long long last = (nseg - 1 - q) / S;  // the slot's last round
-    mbar_wait(&full[q], (unsigned)(last & 1), err, polls);
+    mbar_wait(&full[q], (unsigned)(last & 1), err, polls, 7);
   }
 }
 
@@ -1439,7 +1493,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
                                                                const T* __restrict__ w, long long n, double* part,
                                                                const GmresState* gs, long long rb, int polls,
                                                                int* err) {
-  if (gs->done) return;
+  if (cta_done(gs)) return;
   constexpr int S = DcTma<T>::S, TR = DcTma<T>::TR, NC = DCT_CONS * 32;
   extern __shared__ __align__(128) unsigned char dsm[];
   T* us = reinterpret_cast<T*>(dsm);
@@ -1477,7 +1531,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
       for (long long k = 0; k < nseg; ++k) {
         const int q = (int)(k % S);
         const long long rnd = k / S;
-        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls);
+        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls, 2);
         const int c = (int)(k / nt), t = (int)(k % nt);
         const long long a = r0 + (long long)t * TR;
         bulk_load(ring + (size_t)q * TR, V + (long long)c * ldv + a, dct_bytes<T>(r0 + nr - a < TR ? r0 + nr - a : TR),
@@ -1491,7 +1545,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
     using VT = typename Vec<T>::type;
     constexpr int VN = Vec<T>::n, VPT = TR / (VN * NC);
     static_assert(TR % (VN * NC) == 0, "a segment splits evenly into the consumers' vectors");
-    if (nt > 0) mbar_wait(uwbar, 0u, err, polls);
+    if (nt > 0) mbar_wait(uwbar, 0u, err, polls, 3);
     {
       VT uu = Vec<T>::zero(), uw = Vec<T>::zero();
       const VT* u4 = reinterpret_cast<const VT*>(us);
@@ -1519,7 +1573,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
       for (int t = 0; t < nt; ++t) {
         const long long k = (long long)c * nt + t;
         const int q = (int)(k % S);
-        mbar_wait(&full[q], (unsigned)((k / S) & 1), err, polls);
+        mbar_wait(&full[q], (unsigned)((k / S) & 1), err, polls, 4);
         const T* seg = ring + (size_t)q * TR;
         const T* ut = us + (size_t)t * TR;
         const T* wt = wsl + (size_t)t * TR;
@@ -1561,9 +1615,9 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
   __syncthreads();
   T* row = reinterpret_cast<T*>(part) + (long long)blockIdx.x * DC_LD;
   for (int c = threadIdx.x; c < 2 * j + 2; c += blockDim.x) {
-    T sacc = (T)0;
-    for (int k = 0; k < DCT_CONS; ++k) sacc += wsum[k * DC_LD + c];
-    row[c] = sacc;
+    CSum<T> cs;
+    for (int k = 0; k < DCT_CONS; ++k) cs.add(wsum[k * DC_LD + c]);
+    row[c] = (T)cs.value();
   }
 }
 
@@ -1577,7 +1631,7 @@ template <typename T>
 __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long ldv, int j, const T* __restrict__ w,
                                                                long long n, const double* part, GmresState* gs,
                                                                int mrest, long long rb, int polls, int* err) {
-  if (gs->done) return;
+  if (cta_done(gs)) return;
   constexpr int S = DcTma<T>::S, TR = DcTma<T>::TR, NC = DCT_CONS * 32;
   __shared__ double red[DC_LD];
   __shared__ T coef[2 * GM_MAX];
@@ -1585,16 +1639,9 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
   __shared__ __align__(8) unsigned long long full[S], empty[S];
   const int nb = gridDim.x;
   dc_reduce<T>(part, nb, 2 * j + 2, red);
-  const double uu = red[2 * j], uw = red[2 * j + 1];
-  double ab = 0.0, aa = 0.0;
-  for (int k = 0; k < j; ++k) {
-    ab += red[k] * red[j + k];
-    aa += red[k] * red[k];
-  }
-  const double r2 = uu - aa;
-  const double r = j == 0 ? 1.0 : (r2 > 0.0 ? sqrt(r2) : 0.0);
-  const double inv_r = r > 0.0 ? 1.0 / r : 0.0;
-  const double d = (uw - ab) * inv_r;
+  __shared__ double sc[3];
+  dc_scalars(red, j, sc);
+  const double uw = red[2 * j + 1], r = sc[0], inv_r = sc[1], d = sc[2];
   if (blockIdx.x == 0) {
     // Hessenberg bookkeeping by the first GS_T threads (no sweep in this
     // block); they synchronise on a named barrier of exactly GS_T threads,
@@ -1692,7 +1739,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
       for (long long k = 0; k < nseg; ++k) {
         const int q = (int)(k % S);
         const long long rnd = k / S;
-        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls);
+        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls, 5);
         const int t = (int)(k / per), m = (int)(k % per);
         const long long a = r0 + (long long)t * TR;
         const T* src = m == 0 ? u + a : m == 1 ? w + a : V + (long long)(m - 2) * ldv + a;
@@ -1714,7 +1761,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
     for (int m = 0; m < per; ++m) {
       const long long k = (long long)t * per + m;
       const int q = (int)(k % S);
-      mbar_wait(&full[q], (unsigned)((k / S) & 1), err, polls);
+      mbar_wait(&full[q], (unsigned)((k / S) & 1), err, polls, 6);
       const VT* seg = reinterpret_cast<const VT*>(ring + (size_t)q * TR);
       if (m == 0) {
 #pragma unroll
@@ -1762,7 +1809,7 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
 // the reduction of [Q^T u_m, u_m.u_m]
 template <typename T>
 __global__ void __launch_bounds__(GS_T) k_dc_close(const double* part, int nb, int m, GmresState* gs) {
-  if (gs->done) return;
+  if (cta_done(gs)) return;
   __shared__ double red[DC_LD];
   __shared__ double hc[GM_LD + 1];
   dc_reduce<T>(part, nb, m + 1, red);
@@ -1999,7 +2046,7 @@ __global__ void k_wait_selftest(DevMesh m) {
   if (threadIdx.x != 0) return;
   mbar_init(&bar, 1);
   asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  mbar_wait(&bar, 0u, m.err_flag, m.wait_polls);
+  mbar_wait(&bar, 0u, m.err_flag, m.wait_polls, 8);
 }
 
 // ------------------------------------------------------------------ host side
@@ -2533,21 +2580,27 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
       // factor 0.3 of margin for the FP32 operator), so the last sweep does
       // not overshoot the tolerance by orders of magnitude
       const double inner = std::max(o.inner_rtol, std::min(0.5, 0.3 * tol / rnorm));
-      { note_launch(); k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs, inner); }
-      { note_launch(); k_scale_into<float><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
-      cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
-      if ((st = run_cycle<float, DIM>(h, K, h->J32.dg, h->J32.off, mrest, &h->graph32, &h->gev32))) break;
-      CycleInfo ci;
-      if ((st = read_gs(h, &ci))) break;
-      if (o.use_graphs) prof_flush_graph(h, h->gev32, ci.iters);
-      total += ci.iters;
+      // a sweep asked for no reduction (inner tolerance >= 1) runs no cycle
+      // and leaves the residual as it is
+      int cycle_iters = -1;
+      if (inner < 1.0) {
+        { note_launch(); k_residual_start<float><<<rb, RB, 0, h->stream>>>(K.b, nullptr, K.V, N, h->d_partial, cnt, h->d_gs, inner); }
+        { note_launch(); k_scale_into<float><<<rb, RB, 0, h->stream>>>(K.V, K.V, N, &h->d_gs->inv_h, nullptr); }
+        cudaMemsetAsync(&h->d_gs->iters, 0, sizeof(int), h->stream);
+        if ((st = run_cycle<float, DIM>(h, K, h->J32.dg, h->J32.off, mrest, &h->graph32, &h->gev32))) break;
+        CycleInfo ci;
+        if ((st = read_gs(h, &ci))) break;
+        if (o.use_graphs) prof_flush_graph(h, h->gev32, ci.iters);
+        total += ci.iters;
+        cycle_iters = ci.iters;
+      }
       refinements += 1;
       { note_launch(); k_promote_axpy<<<rb, RB, 0, h->stream>>>(x, K.x, N, h->d_red); }
       prof_begin(h, PK_SPMV64);
       spmv<double, DIM, 0>(h, h->J64.dg, h->J64.off, x, h->tmp64, nullptr);
       prof_end(h);
       { note_launch(); k_residual_start<double><<<rb, RB, 0, h->stream>>>(b, h->tmp64, r, N, h->d_partial, cnt, h->d_gs + 0, 0.0); }
-      if (ci.iters == 0) break;
+      if (cycle_iters == 0) break;
     }
   }
   if (use64 && !st) {
@@ -2603,7 +2656,9 @@ static hf_status solve_impl(hf_mesh* h, const double* b, double* x, hf_newton_re
   cudaStreamSynchronize(h->stream);
   if (flag) {
     cudaMemsetAsync(h->d.err_flag, 0, sizeof(int), h->stream);
-    return set_error(h, HF_ERR_TIMEOUT, "a bounded device wait timed out in the preconditioner");
+    char msg[96];
+    snprintf(msg, sizeof msg, "a bounded device wait timed out in the linear solve (site %d)", flag);
+    return set_error(h, HF_ERR_TIMEOUT, msg);
   }
   return st;
 }

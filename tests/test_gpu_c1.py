@@ -96,19 +96,24 @@ def test_c1_newton_step_matches_oracle(extra):
     """One FP64 Newton iteration of the c1 mesh (46,553 unknowns) from the
     same state on both sides, the seed alone or with two more cohesive
     facets in the softening branch: U and P within 1e-10 of the oracle's
-    step (GMRES to 1e-13, the oracle's direct solve refined)."""
+    step (the oracle's direct solve refined).  The GMRES tolerance is 1e-14:
+    the increment's error is the linear solve's residual amplified by the
+    conditioning of the scaled system (about 1e3 here), and 1e-13 left
+    1.1e-10 from the seed state; a solve that stagnates within a decade of
+    1e-14 (the attainable accuracy of FP64 GMRES) is accepted, as the time
+    loop does."""
     wl = c1_kgd_toughness()
     state = wl.seed()
     if extra:
         state, _ = with_extra_cohesive(wl, state, count=extra)
     o = oracle_for(wl, cutoff=True)
     o.set_state(*state)
-    g = gpu_for(wl, cutoff=True, precision="fp64", rtol=1e-13, max_iters=20000, jacobi_block=16)
+    g = gpu_for(wl, cutoff=True, precision="fp64", rtol=1e-14, max_iters=40000, jacobi_block=16)
     g.hf_set_state(*state)
     rep = g.hf_newton_step()
     o.newton_step()
     Ug, Pg = g.hf_get_state()[:2]
     g.close()
-    assert rep["lin_converged"], rep
+    assert rep["lin_converged"] or rep["lin_res"] <= 1e-13, rep
     assert rel_err(Ug, o.U) <= 1e-10
     assert rel_err(Pg, o.P) <= 1e-10
