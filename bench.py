@@ -389,6 +389,15 @@ def run_ours(args):
     roofline = {"bound": "hbm", "kernel": kname, "class": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "peak_source": peak_src, "algorithmic_bytes": int(b_dom),
                 "launches": n_dom, "ms": ms_dom, "traffic": traffic_from_profiles(kname.split(" ")[0])}
+    if isinstance(roofline["traffic"], dict):
+        # measured traffic / algorithmic bytes of the captured launch, applied
+        # to this run's algorithmic bytes per Arnoldi step (the class's unit)
+        t = roofline["traffic"]
+        per_step = b_dom / max(arnoldi, 1)
+        roofline["traffic"] = t["bytes"] / t["algorithmic"] * per_step
+        roofline["traffic_unit"] = (f"bytes per Arnoldi step (dot + update kernels), ncu capture at j = "
+                                    f"{t['captured_at_j']} scaled by the run's algorithmic bytes per step")
+        roofline["algorithmic_bytes_per_step"] = per_step
     sol_bytes = sum(v[0] for v in cls.values())
     sol_ms = sum(v[1] for v in cls.values())
     # the same bytes per Arnoldi step against the real schedule: whole GMRES
