@@ -1252,21 +1252,25 @@ __global__ void __launch_bounds__(GS_T) k_dc_dot(const T* __restrict__ V, long l
 // DC_SLAB values at a time, four independent loads per thread and pass),
 // then G threads per column add interleaved rows and their G partial sums
 // meet in a fixed order: the same order, hence the same result, in every CTA
-template <typename RT>
-__device__ void dc_reduce(const double* part_raw, int nb, int nvc, double* out) {
-  extern __shared__ __align__(16) unsigned char stage_raw[];
-  RT* stage = reinterpret_cast<RT*>(stage_raw);
+// (NAMED: run by threads 0 .. GS_T-1 alone, on named barrier 1, while a
+// producer warp of the CTA streams; otherwise by the whole CTA)
+template <bool NAMED> __device__ __forceinline__ void dc_sync() {
+  if (NAMED) asm volatile("bar.sync 1, %0;" ::"n"(GS_T) : "memory");
+  else __syncthreads();
+}
+template <typename RT, bool NAMED = false>
+__device__ void dc_reduce(const double* part_raw, int nb, int nvc, double* out, RT* stage) {
   const RT* part = reinterpret_cast<const RT*>(part_raw);
   __shared__ double gpart[GS_T];
   const int rows_per = max(1, DC_SLAB / max(nvc, 1));
-  const int nth = min((int)blockDim.x, GS_T);  // threads past GS_T only join the barriers
+  const int nth = NAMED ? GS_T : min((int)blockDim.x, GS_T);  // threads past GS_T only join the barriers
   const int G = max(1, min(8, nth / max(nvc, 1)));
   const int c = threadIdx.x % max(nvc, 1), g = (int)threadIdx.x < nth ? threadIdx.x / max(nvc, 1) : G;
   CSum<RT> acc;
   for (int r0 = 0; r0 < nb; r0 += rows_per) {
     const int nr = min(rows_per, nb - r0);
     const int tot = nr * nvc;
-    __syncthreads();
+    dc_sync<NAMED>();
     for (int t = threadIdx.x; t < tot; t += 4 * nth) {
       if ((int)threadIdx.x >= nth) break;
       RT v[4];
@@ -1283,18 +1287,18 @@ __device__ void dc_reduce(const double* part_raw, int nb, int nvc, double* out) 
       for (int k = 0; k < 4; ++k)
         if (t + k * nth < tot) stage[t + k * nth] = v[k];
     }
-    __syncthreads();
+    dc_sync<NAMED>();
     if (g < G)
       for (int rr = g; rr < nr; rr += G) acc.add(stage[rr * nvc + c]);
   }
   if (g < G) gpart[g * nvc + c] = acc.value();
-  __syncthreads();
+  dc_sync<NAMED>();
   for (int cc = threadIdx.x; cc < nvc; cc += nth) {
     double t = 0.0;
     for (int k = 0; k < G; ++k) t += gpart[k * nvc + cc];
     out[cc] = t;
   }
-  __syncthreads();
+  dc_sync<NAMED>();
 }
 
 // r = sqrt(u.u - a.a), 1 / r and d = (u.w - a.b) / r of the delayed CGS2
@@ -1302,7 +1306,7 @@ __device__ void dc_reduce(const double* part_raw, int nb, int nvc, double* out) 
 // then a fixed butterfly), the block reads the three numbers from shared
 // memory.  Every CTA computes them in the same order, hence identically;
 // one warp instead of every thread, because FP64 arithmetic is scarce here.
-__device__ void dc_scalars(const double* red, int j, double* sc) {
+template <bool NAMED = false> __device__ void dc_scalars(const double* red, int j, double* sc) {
   if (threadIdx.x < 32) {
     double ab = 0.0, aa = 0.0;
     for (int k = threadIdx.x; k < j; k += 32) {
@@ -1320,7 +1324,7 @@ __device__ void dc_scalars(const double* red, int j, double* sc) {
       sc[2] = (red[2 * j + 1] - ab) * inv_r;
     }
   }
-  __syncthreads();
+  dc_sync<NAMED>();
 }
 
 // Givens rotations of the final column jc (hc, jc + 2 entries, rotated in
@@ -1366,7 +1370,8 @@ __global__ void __launch_bounds__(GS_T) k_dc_upd(T* V, long long ldv, int j, con
   __shared__ double hc[GM_LD + 1], cvec[GM_LD];
   const int nb = gridDim.x;
   const int nvc = 2 * j + 2;
-  dc_reduce<T>(part, nb, nvc, red);
+  extern __shared__ __align__(16) unsigned char dc_stage[];
+  dc_reduce<T>(part, nb, nvc, red, reinterpret_cast<T*>(dc_stage));
   __shared__ double sc[3];
   dc_scalars(red, j, sc);
   const double uw = red[2 * j + 1], r = sc[0], inv_r = sc[1], d = sc[2];
@@ -1626,7 +1631,10 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_dot_tma(const T* __restri
 // j final basis vectors; each consumer thread keeps its rows' two running
 // sums in registers and writes v_j and the next lagged vector at the end of
 // the tile.  Block 0 keeps the Hessenberg bookkeeping, as in k_dc_upd; the
-// other CTAs share the rows (slices of rb rows).
+// other CTAs share the rows (slices of rb rows).  The producer warp starts
+// streaming at once (the copies need nothing from the reduction) while the
+// consumer warps reduce the table in a staging area beside the ring, on a
+// named barrier of their own.
 template <typename T>
 __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long ldv, int j, const T* __restrict__ w,
                                                                long long n, const double* part, GmresState* gs,
@@ -1637,16 +1645,48 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
   __shared__ T coef[2 * GM_MAX];
   __shared__ double hc[GM_LD + 1], cvec[GM_LD];
   __shared__ __align__(8) unsigned long long full[S], empty[S];
-  const int nb = gridDim.x;
-  dc_reduce<T>(part, nb, 2 * j + 2, red);
   __shared__ double sc[3];
-  dc_scalars(red, j, sc);
+  extern __shared__ __align__(128) unsigned char dsm[];
+  T* ring = reinterpret_cast<T*>(dsm);
+  T* stage = ring + (size_t)S * TR;  // dc_reduce's staging area
+  const int nb = gridDim.x;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long r0 = (long long)(blockIdx.x - 1) * rb;
+  const long long nr = blockIdx.x > 0 && r0 < n ? (n - r0 < rb ? n - r0 : rb) : 0;
+  const int nt = (int)((nr + TR - 1) / TR);
+  const int per = j + 2;  // segments per tile: u_j, w, Q_0 .. Q_{j-1}
+  T* u = V + (long long)j * ldv;
+  T* un = V + (long long)(j + 1) * ldv;
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < S; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], DCT_CONS);
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  if (warp == DCT_CONS) {
+    if (lane == 0) {
+      const long long nseg = (long long)nt * per;
+      for (long long k = 0; k < nseg; ++k) {
+        const int q = (int)(k % S);
+        const long long rnd = k / S;
+        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls, 5);
+        const int t = (int)(k / per), m = (int)(k % per);
+        const long long a = r0 + (long long)t * TR;
+        const T* src = m == 0 ? u + a : m == 1 ? w + a : V + (long long)(m - 2) * ldv + a;
+        bulk_load(ring + (size_t)q * TR, src, dct_bytes<T>(r0 + nr - a < TR ? r0 + nr - a : TR), &full[q]);
+      }
+    }
+    return;
+  }
+  // consumers: threads 0 .. GS_T-1, synchronised on named barrier 1
+  dc_reduce<T, true>(part, nb, 2 * j + 2, red, stage);
+  dc_scalars<true>(red, j, sc);
   const double uw = red[2 * j + 1], r = sc[0], inv_r = sc[1], d = sc[2];
   if (blockIdx.x == 0) {
-    // Hessenberg bookkeeping by the first GS_T threads (no sweep in this
-    // block); they synchronise on a named barrier of exactly GS_T threads,
-    // the producer warp leaves
-    if (threadIdx.x >= GS_T) return;
+    // Hessenberg bookkeeping by the consumer threads (no sweep in this
+    // block; its producer issued nothing)
     if (j == 0) {
       if (threadIdx.x == 0) gs->Hr[0] = uw;
       return;
@@ -1708,46 +1748,11 @@ __global__ void __launch_bounds__(DCT_THREADS, 1) k_dc_upd_tma(T* V, long long l
     }
     return;
   }
-  for (int k = threadIdx.x; k < j; k += blockDim.x) {
+  for (int k = threadIdx.x; k < j; k += GS_T) {
     coef[k] = (T)red[k];
     coef[GM_MAX + k] = (T)red[j + k];
   }
-  // the staging area of dc_reduce becomes the ring
-  extern __shared__ __align__(128) unsigned char dsm[];
-  T* ring = reinterpret_cast<T*>(dsm);
-  if (threadIdx.x == 0) {
-    for (int q = 0; q < S; ++q) {
-      mbar_init(&full[q], 1);
-      mbar_init(&empty[q], DCT_CONS);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-  }
-  // the ring reuses dc_reduce's staging area: order its generic reads before
-  // the first asynchronous copy into it
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-  __syncthreads();
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long r0 = (long long)(blockIdx.x - 1) * rb;
-  const long long nr = r0 < n ? (n - r0 < rb ? n - r0 : rb) : 0;
-  const int nt = (int)((nr + TR - 1) / TR);
-  const int per = j + 2;  // segments per tile: u_j, w, Q_0 .. Q_{j-1}
-  T* u = V + (long long)j * ldv;
-  T* un = V + (long long)(j + 1) * ldv;
-  if (warp == DCT_CONS) {
-    if (lane == 0) {
-      const long long nseg = (long long)nt * per;
-      for (long long k = 0; k < nseg; ++k) {
-        const int q = (int)(k % S);
-        const long long rnd = k / S;
-        if (rnd > 0) mbar_wait(&empty[q], (unsigned)((rnd - 1) & 1), err, polls, 5);
-        const int t = (int)(k / per), m = (int)(k % per);
-        const long long a = r0 + (long long)t * TR;
-        const T* src = m == 0 ? u + a : m == 1 ? w + a : V + (long long)(m - 2) * ldv + a;
-        bulk_load(ring + (size_t)q * TR, src, dct_bytes<T>(r0 + nr - a < TR ? r0 + nr - a : TR), &full[q]);
-      }
-    }
-    return;
-  }
+  sync_gs();
   // each consumer thread owns VPT vectors of every tile; it loads the whole
   // vector even past the slice's last row (the ring slot is TR long, the
   // values there are never stored)
@@ -1812,7 +1817,8 @@ __global__ void __launch_bounds__(GS_T) k_dc_close(const double* part, int nb, i
   if (cta_done(gs)) return;
   __shared__ double red[DC_LD];
   __shared__ double hc[GM_LD + 1];
-  dc_reduce<T>(part, nb, m + 1, red);
+  extern __shared__ __align__(16) unsigned char dc_stage[];
+  dc_reduce<T>(part, nb, m + 1, red, reinterpret_cast<T*>(dc_stage));
   double aa = 0.0;
   for (int k = 0; k < m; ++k) aa += red[k] * red[k];
   const double r2 = red[m] - aa;
@@ -2176,6 +2182,12 @@ template <typename T> static void dc_configure() {
   });
 }
 
+// dynamic shared memory of the streamed delayed CGS2 update kernel: the ring
+// and, beside it, the staging area of its table reduction
+template <typename T> static size_t dct_upd_smem() {
+  return (size_t)DcTma<T>::S * DcTma<T>::TR * sizeof(T) + (size_t)DC_SLAB * sizeof(T);
+}
+
 // dynamic shared memory of the streamed delayed CGS2 dot kernel for slices
 // of rb rows (u and w of the slice, the ring, the per-warp sums, barriers),
 // or 0 when it does not fit beside the kernel's static shared memory
@@ -2381,7 +2393,7 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
       if (dsm) {
         // the basis streamed through shared memory by bulk copies
         { note_launch(); k_dc_dot_tma<T><<<nb, DCT_THREADS, dsm, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, (rb_dot + 63) / 64 * 64, h->d.wait_polls, h->d.err_flag); }
-        { note_launch(); k_dc_upd_tma<T><<<nb, DCT_THREADS, std::max(DC_SMEM, (size_t)DcTma<T>::S * DcTma<T>::TR * sizeof(T)), h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, mrest, (rb_upd + 63) / 64 * 64, h->d.wait_polls, h->d.err_flag); }
+        { note_launch(); k_dc_upd_tma<T><<<nb, DCT_THREADS, dct_upd_smem<T>(), h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, mrest, (rb_upd + 63) / 64 * 64, h->d.wait_polls, h->d.err_flag); }
       } else {
         { note_launch(); k_dc_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs); }
         { note_launch(); k_dc_upd<T><<<nb, GS_T, DC_SMEM, h->stream>>>(K.V, K.ldv, j, K.w, N, h->d_partial, gs, mrest); }
