@@ -153,23 +153,55 @@ def toughness_consistent(wl: Workload, sigma_c_max=1e6, zone_elems=4.0) -> Workl
     return dataclasses.replace(out, L_ref=balanced_fluid_length(out))
 
 
+def toughness_vertex_size(wl: Workload, t: float) -> float:
+    """Half-length (2D) or radius (3D) at time t of the seed crack grown as
+    the toughness vertex with no leak-off: the volume V0 + Q0 t held at
+    K_I = K_Ic (plane strain: V = 2 sqrt(pi) K_Ic l^(3/2) / E'; penny:
+    V = 8 sqrt(pi) K_Ic R^(5/2) / (3 E')), V0 the seed's volume at its
+    toughness.  For the same volume a viscous crack is shorter, so this
+    bounds the crack's size from above."""
+    Ep = wl.E / (1.0 - wl.nu ** 2)
+    a = wl.seed_radius
+    if wl.mesh.dim == 2:
+        return (a ** 1.5 + Ep * wl.Q0 * t / (2.0 * math.sqrt(math.pi) * wl.K_Ic)) ** (2.0 / 3.0)
+    return (a ** 2.5 + 3.0 * Ep * wl.Q0 * t / (8.0 * math.sqrt(math.pi) * wl.K_Ic)) ** 0.4
+
+
+def crack_stays_inside(wl: Workload, steps: int, frac: float = 0.6) -> bool:
+    """True when the crack's size bound after `steps` steps of dt stays
+    within frac of the half-domain: the paper's tests keep the domain much
+    larger than the crack, and a draw whose crack would reach the boundary
+    within the run is not an instance of them."""
+    return toughness_vertex_size(wl, steps * wl.dt) <= frac * 0.5 * wl.mesh.length
+
+
 def sweep_instances(count=256, seed=191110275, ne_range=(1000, 50000), steps=10, mesh_cache=None):
     """Batched 2D KGD sweep: `count` independent plane-strain instances with
     the draws of batch_instances (element count, E, K_Ic, mu, Q0 log-uniform),
     nu = 0.2, sigma_c = 1 MPa at most, crack on the midline, seed and sigma_c
-    from toughness_consistent.  Meshes of equal n are shared through
-    mesh_cache (a dict)."""
+    from toughness_consistent; a draw whose crack could reach the boundary
+    within the run (crack_stays_inside) is replaced by a fresh draw of E,
+    K_Ic, mu and Q0.  Meshes of equal n are shared through mesh_cache (a
+    dict)."""
     cache = {} if mesh_cache is None else mesh_cache
     out = []
-    for i, d in enumerate(batch_instances(count, seed, ne_range)):
+    draws = batch_instances(count, seed, ne_range)
+    rng = np.random.Generator(np.random.PCG64(seed + 1))   # redraws of E, K_Ic, mu, Q0
+    for i, d in enumerate(draws):
         n = d["n"]
         key = ("kgd", n)
         if key not in cache:
             cache[key] = square_p2(n, 100.0, crackable="midline")
         h = 100.0 / n
-        out.append(toughness_consistent(
-            Workload(f"sweep{i}_kgd2d_n{n}", cache[key], d["E"], 0.2, d["K_Ic"], 1e6, d["mu"], d["Q0"], 1.0,
-                     steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6)))
+        prm = {k: d[k] for k in ("E", "K_Ic", "mu", "Q0")}
+        for _ in range(100):
+            wl = toughness_consistent(
+                Workload(f"sweep{i}_kgd2d_n{n}", cache[key], prm["E"], 0.2, prm["K_Ic"], 1e6, prm["mu"], prm["Q0"],
+                         1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6))
+            if crack_stays_inside(wl, steps):
+                break
+            prm = sample_parameters(rng)
+        out.append(wl)
     return out
 
 
@@ -181,29 +213,43 @@ def serving_requests(count=2000, rate=200.0, seed=191110275, kgd_n=(50, 316), pe
     penny_n, crack plane z = 0), parameters from sample_parameters (nu = 0.2
     for KGD, 0.25 for the penny), `steps` time steps each from the seed
     state; seed and sigma_c (at most 1 MPa for KGD, 0.3 MPa for the penny)
-    from toughness_consistent.  Returns (arrival times in s, workloads)."""
+    from toughness_consistent; a draw whose crack could reach the boundary
+    within the request (crack_stays_inside) is replaced by a fresh draw.
+    Returns (arrival times in s, workloads)."""
     rng = np.random.default_rng(seed)
     cache = {} if mesh_cache is None else mesh_cache
     t = np.cumsum(rng.exponential(1.0 / rate, size=count))
     out = []
     for i in range(count):
         prm = sample_parameters(rng)
-        if rng.uniform() < 0.5:
+        kgd = rng.uniform() < 0.5
+        if kgd:
             n = _even(math.exp(rng.uniform(math.log(kgd_n[0]), math.log(kgd_n[1]))), kgd_n[0], kgd_n[1])
             key = ("kgd", n)
             if key not in cache:
                 cache[key] = square_p2(n, 100.0, crackable="midline")
             h = 100.0 / n
-            out.append(toughness_consistent(
-                Workload(f"req{i}_kgd2d_n{n}", cache[key], prm["E"], 0.2, prm["K_Ic"], 1e6, prm["mu"], prm["Q0"], 1.0,
-                         steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6)))
+
+            def make(prm):
+                return toughness_consistent(
+                    Workload(f"req{i}_kgd2d_n{n}", cache[key], prm["E"], 0.2, prm["K_Ic"], 1e6, prm["mu"], prm["Q0"],
+                             1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=1e-3, p0=1e6))
         else:
             n = _even(math.exp(rng.uniform(math.log(penny_n[0]), math.log(penny_n[1]))), penny_n[0] + 1, penny_n[1])
             key = ("penny", n)
             if key not in cache:
                 cache[key] = cube_p2(n, 50.0, crackable="plane")
             h = 50.0 / n
-            out.append(toughness_consistent(
-                Workload(f"req{i}_penny3d_n{n}", cache[key], prm["E"], 0.25, prm["K_Ic"], 0.3e6, prm["mu"], prm["Q0"],
-                         1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=2e-3, p0=1e6), sigma_c_max=0.3e6))
+
+            def make(prm):
+                return toughness_consistent(
+                    Workload(f"req{i}_penny3d_n{n}", cache[key], prm["E"], 0.25, prm["K_Ic"], 0.3e6, prm["mu"],
+                             prm["Q0"], 1.0, steps=steps, seed_radius=2 * h * 1.0001, w0=2e-3, p0=1e6),
+                    sigma_c_max=0.3e6)
+        wl = make(prm)
+        for _ in range(100):
+            if crack_stays_inside(wl, steps):
+                break
+            wl = make(sample_parameters(rng))
+        out.append(wl)
     return t, out
