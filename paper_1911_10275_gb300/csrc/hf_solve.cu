@@ -375,8 +375,8 @@ template <typename T, int DIM>
 __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __restrict__ dg,
                                                     const double* __restrict__ off, T* lu, const int* sdlist) {
   using S = Shape<DIM>;
-  constexpr int NED = S::ned, NFR = S::nfr, LUS = S::lus;
-  extern __shared__ __align__(16) unsigned char smraw[];
+  constexpr int NED = S::ned, NFR = S::nfr;
+  extern __shared__ __align__(128) unsigned char smraw[];
   int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   T* Am = reinterpret_cast<T*>(smraw) + warp * (NED * NED + NFR * NED);
   T* Lm = Am + NED * NED;
@@ -413,7 +413,7 @@ __global__ void __launch_bounds__(128) k_ilu_factor(DevMesh m, const double* __r
         if ((nlm >> j) & 1u) cohesive_patch_rows<T, DIM>(m, i, j, 1, Lm, NED, false, lane);
         __syncwarp();
         // L_ik = A_ik Dinv_k
-        const unsigned low_k = m.lowmask[k], up_k = m.upmask[k];
+        const unsigned up_k = m.upmask[k];
         const T* reckb = lu + m.rec_bwd[k];
         const T* dk = reckb + nbits(up_k) * NED * NFR;
         T lrow[NED];
@@ -484,7 +484,7 @@ template <typename T, int DIM>
 __global__ void k_schur(DevMesh m, const T* __restrict__ lu, T* sinv) {
   using S = Shape<DIM>;
   using L = NL<DIM>;
-  constexpr int F = S::nfn, NED = S::ned, LUS = S::lus;
+  constexpr int F = S::nfn, NED = S::ned;
   int g = blockIdx.x * blockDim.x + threadIdx.x;
   if (g >= m.np) return;
   if (!m.p_active[g] || m.p_fixval[g] == m.p_fixval[g]) {
