@@ -2,6 +2,7 @@
 computed by the library from a descriptor, the replica split of independent
 instances (with a two-rank gloo group), the serving client's bookkeeping and
 the request generators."""
+import math
 import os
 import socket
 
@@ -172,3 +173,37 @@ def test_autotuner_picks_the_fastest_candidate_once_per_size_class(monkeypatch):
     opts = t.solver_for(a, "mixed")
     assert opts["jacobi_block"] == best[0] and opts["restart"] == best[1] and opts["precision"] == "mixed"
     assert set(t.report()) == {"2d/mixed/2^%d" % autotune.size_class(w, "mixed")[2] for w in (a, c)}
+
+
+def test_toughness_vertex_size_bound_against_the_opening_profiles():
+    """The size bound of the instance generators (hf_inputs.workloads):
+    at t = 0 it returns the seed's size; for t > 0 the crack it returns,
+    held at K_I = K_Ic, holds exactly V0 + Q0 t, with the volumes integrated
+    numerically from Sneddon's plane-strain opening 4 p / E' sqrt(l^2 - x^2)
+    and the penny's 8 p R / (pi E') sqrt(1 - r^2 / R^2), p from Irwin's
+    K_I = p sqrt(pi l) and the penny's K_I = 2 p sqrt(R / pi)."""
+    import dataclasses
+    from hf_inputs.workloads import toughness_vertex_size, crack_stays_inside, toughness_consistent
+    from scipy.integrate import quad
+
+    def volume_2d(l, K, Ep):
+        p = K / math.sqrt(math.pi * l)
+        return quad(lambda x: 4 * p / Ep * math.sqrt(l * l - x * x), -l, l)[0]
+
+    def volume_3d(R, K, Ep):
+        p = K * math.sqrt(math.pi) / (2 * math.sqrt(R))
+        return quad(lambda r: 2 * math.pi * r * 8 * p * R / (math.pi * Ep) * math.sqrt(1 - (r / R) ** 2), 0, R)[0]
+
+    for wl, vol in ((toughness_consistent(kgd_2d(n=20, length=40.0, E=17e9, K_Ic=1.5e6, Q0=1e-3)), volume_2d),
+                    (toughness_consistent(penny_3d(n=12, crackable="plane", E=10e9, K_Ic=1e6, Q0=1e-2)), volume_3d)):
+        Ep = wl.E / (1 - wl.nu ** 2)
+        a = wl.seed_radius
+        assert toughness_vertex_size(wl, 0.0) == pytest.approx(a, rel=1e-12)
+        v0 = vol(a, wl.K_Ic, Ep)
+        for t in (0.5, 3.0, 20.0):
+            size = toughness_vertex_size(wl, t)
+            assert vol(size, wl.K_Ic, Ep) == pytest.approx(v0 + wl.Q0 * t, rel=1e-9)
+        # the filter: inside for a short run, outside once the bound passes 0.6 of the half-domain
+        assert crack_stays_inside(wl, 0)
+        far = dataclasses.replace(wl, Q0=wl.Q0 * 1e6)
+        assert not crack_stays_inside(far, 1)
