@@ -191,6 +191,53 @@ def square_p2(n: int, length: float = 100.0, crackable: str = "midline",
                 int(nid(n, n)), 1)
 
 
+def split_triangles(mesh: Mesh, elems, crackable: str = "all") -> Mesh:
+    """The 2D P2 mesh with each listed triangle split at its centroid into
+    three (new vertex and the three new edge mid-nodes appended, the edges
+    of the old triangle and their mid-nodes kept).  The three children share
+    edges pairwise, so the element graph gains triangles: block ILU(0) then
+    has fill between neighbours through a common earlier neighbour.
+    ``crackable`` as in square_p2 ("all" or "midline")."""
+    if mesh.dim != 2:
+        raise ValueError("triangles only")
+    xyz = [tuple(p) for p in mesh.xyz]
+    out = [list(e) for e in mesh.elem_nodes]
+
+    def add(p):
+        xyz.append((float(p[0]), float(p[1])))
+        return len(xyz) - 1
+    for e in sorted(set(int(x) for x in elems)):
+        v = [int(mesh.elem_nodes[e, k]) for k in range(3)]
+        mid = {TRI_EDGES[k]: int(mesh.elem_nodes[e, 3 + k]) for k in range(3)}
+        pv = [np.asarray(mesh.xyz[x]) for x in v]
+        c = add((pv[0] + pv[1] + pv[2]) / 3.0)
+        mc = [add((pv[k] + np.asarray(xyz[c])) / 2.0) for k in range(3)]
+        kids = []
+        for a, b in TRI_EDGES:   # child (v_a, v_b, c), counter-clockwise as its parent
+            m_ab = mid[(a, b)]
+            kids.append([v[a], v[b], c, m_ab, mc[b], mc[a]])
+        out[e] = kids[0]
+        out.extend(kids[1:])
+    elem = np.asarray(out, dtype=np.int64)
+    xyz = np.asarray(xyz, dtype=np.float64)
+    fe, fl = _build_faces(2, elem)
+    crack = np.zeros(fe.shape[0], dtype=np.int8)
+    interior = fe[:, 1] >= 0
+    if crackable == "all":
+        crack[interior] = 1
+    elif crackable == "midline":
+        for f in np.nonzero(interior)[0]:
+            fv = _local_face_vertices(2, int(fl[f, 0]))
+            y = xyz[elem[fe[f, 0], list(fv)], 1]
+            if np.all(np.abs(y) < 1e-9 * mesh.length):
+                crack[f] = 1
+    else:
+        raise ValueError(crackable)
+    dd, dv = _rollers(2, xyz, elem, fe, fl, mesh.length / 2)
+    return Mesh(2, xyz, elem.astype(np.int32), fe, fl, crack, dd, dv, mesh.length, mesh.n,
+                mesh.center_node, mesh.crack_normal_axis)
+
+
 def cube_p2(n: int, length: float = 50.0, crackable: str = "plane") -> Mesh:
     """[-L/2, L/2]^3 split into n^3 cubes, six Kuhn P2 tetrahedra per cube.
 
