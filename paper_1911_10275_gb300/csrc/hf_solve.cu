@@ -2416,8 +2416,6 @@ static void gmres_cycle(hf_mesh* h, Krylov<T>& K, const T* dg, const T* off, int
   }
   if (h->opts.reorth == 3) {
     // a cycle that ran all mrest steps still has its last column to finalise
-    const T* um = K.V + (long long)mrest * K.ldv;
-    (void)um;
     { note_launch(); k_dc_dot<T><<<nb, GS_T, 0, h->stream>>>(K.V, K.ldv, mrest, nullptr, N, h->d_partial, gs); }
     { note_launch(); k_dc_close<T><<<1, GS_T, DC_SMEM, h->stream>>>(h->d_partial, nb, mrest, gs); }
   }
