@@ -668,3 +668,40 @@ def test_staggered_step_is_the_decoupled_block_solve():
     assert np.abs(rp).max() <= 1e-10 * np.abs(R2[Nu:]).max()
     assert np.abs(dP).max() > 0.0
     assert np.all(o.P[fixed] == 0.0)
+
+
+def test_far_field_stress_superposition_on_the_oracle():
+    """Far-field stress (Sec. 4.2) as the traction -sigma0 n on the outer face
+    parallel to the crack: with the cohesive law spent and the crack's
+    pressures held as essential rows, the discrete problem is linear, and a
+    uniform stress is represented exactly by P2 elements, so a crack held at
+    p under the far field opens exactly as the same crack held at p - sigma0
+    without it.  A wrong sign or normal of the Neumann traction, or a traction
+    applied to the wrong face, breaks the identity."""
+    from hf_inputs import far_field_load, kgd_2d
+    wl = kgd_2d(n=8, length=16.0, crackable="midline", seed_cells=2)
+    sigma0, p = 2e6, 5e6
+
+    def solve(s0, pc):
+        m, nf, tr = far_field_load(wl.mesh, s0)
+        pn = pressure_nodes(m)
+        U, P, al, be = wl.seed()
+        inj, wts = wl.injection()
+        prm = Params(E=wl.E, nu=wl.nu, sigma_c=1e6, delta_c=1e-12, b_stab=10.0, mu=wl.mu, Q0=0.0,
+                     inj_pdofs=tuple(inj), inj_weights=tuple(wts), delta_f=1e-12, dt=1.0, L_ref=wl.fluid_length,
+                     newton_tol=1e-10, fixed_pdofs=tuple(range(pn.size)), fixed_pvals=tuple([pc] * pn.size))
+        o = Oracle(m, prm, neu_faces=nf, neu_traction=tr)
+        o.set_state(U, np.full(pn.size, pc), al, be)
+        for _ in range(6):
+            if o.newton_step()["converged"]:
+                break
+        crack = np.nonzero(m.face_crackable & (al > 0))[0]
+        return o.opening_at_face_nodes(o.U)[crack], nf, tr
+    wa, nf, tr = solve(sigma0, p)
+    wb, _, _ = solve(0.0, p - sigma0)
+    assert len(nf) > 0 and np.all(tr[:, wl.mesh.crack_normal_axis] == -sigma0)
+    assert np.abs(wa).max() > 0.0
+    assert np.abs(wa - wb).max() <= 1e-9 * np.abs(wb).max()
+    # the far field closes the crack: the same pressure opens it less
+    wc, _, _ = solve(0.0, p)
+    assert wc.sum() > wa.sum()
