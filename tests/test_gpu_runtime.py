@@ -201,3 +201,30 @@ def test_bounded_device_wait_gives_up_with_timeout_status():
     rep = g.hf_newton_step()
     assert rep["lin_converged"]
     g.close()
+
+
+def test_runtime_request_matches_oracle_time_loop():
+    """One small request through the request loop (hf_runtime_*: copy-in,
+    admission, hf_advance_step per step on a slot's stream, copy-out) ends
+    where the oracle's time loop ends: three steps of the small KGD problem
+    of test_advance_step_matches_oracle_time_loop (cutbacks in the second),
+    facet states equal, U, pressures and face-node openings within 1e-9."""
+    from paper_1911_10275_gb300 import HFRuntime
+    from paper_1911_10275_gb300.serving import request_args
+    wl = kgd_2d(n=8, length=16.0, steps=3, seed_cells=2)
+    o = oracle_for(wl)
+    o.set_state(*wl.seed())
+    for _ in range(3):
+        oracle_advance_step(o)
+    rt = HFRuntime(slots=1)
+    args = {**request_args(wl), "cutoff_on": False}
+    rid = rt.submit(wl.mesh, n_steps=3, solver={"precision": "fp64", "rtol": 1e-13, "max_iters": 20000,
+                                                "jacobi_block": 16}, **args)
+    r = rt.wait(rid, timeout=300.0)
+    assert r is not None and r["status"] == 0 and r["steps_done"] == 3, r
+    U, P, a, b = rt.fetch(rid, r)
+    rt.close()
+    assert np.array_equal(a, o.alpha) and np.array_equal(b, o.beta)
+    assert rel_err(U, o.U) < 1e-9
+    assert rel_err(P, o.P) < 1e-9
+    assert rel_err(o.opening_at_face_nodes(U), o.opening_at_face_nodes(o.U)) < 1e-9
