@@ -95,7 +95,7 @@ def oracle_advance_step(o, newton_max=8, rounds_max=4, max_cutbacks=10, newton=N
                 rec["rounds"].append(it)
                 rec["switched"].append(int(n_new))
                 if max_new_facets > 0 and n_new > max_new_facets:
-                    it = None      # this round is recorded already
+                    it = None      # its Newton count is in rec["rounds"] already
                     break
                 if n_new == 0 or rounds >= rounds_max:
                     ok = True
