@@ -224,6 +224,7 @@ class Params:
     newton_maxit: int = 25
     fixed_pdofs: tuple = ()        # pressure DOFs held at fixed_pvals (an essential condition)
     fixed_pvals: tuple = ()
+    beta_connected: bool = False   # fluid enters a failed facet only from a fluid-filled neighbour
 
 
 class Oracle:
@@ -264,6 +265,7 @@ class Oracle:
         self.P = np.zeros(self.Np)
         self.alpha = np.zeros(self.nf, dtype=np.int8)
         self.beta = np.zeros(self.nf, dtype=np.int8)
+        self.spent = np.zeros(self.nf, dtype=np.int8)   # 1: a crack whose cohesive law is spent (dry crack)
         self.w_old = np.zeros((self.nf, self.nfn))
         self.t = 0.0
         self.c_scale = 1.0
@@ -381,10 +383,15 @@ class Oracle:
 
     def tsl(self, w, f):
         """Traction-separation law (Eq. tsl) with the readings: zero traction
-        beyond delta_c, contact penalty (b/h)(lambda+2mu) for w < 0."""
+        beyond delta_c, contact penalty (b/h)(lambda+2mu) for w < 0.  On a
+        spent facet (a pre-existing dry crack, Sec. 4.5) the law has no
+        strength left: zero traction in opening, the same contact penalty in
+        closure (continuous at w = 0)."""
         p = self.prm
         lam, mu = lame(p.E, p.nu)
         kp = p.b_stab / self.hf[f] * (lam + 2 * mu)
+        if self.spent[f]:
+            return np.where(w < 0.0, kp * w, 0.0), np.where(w < 0.0, kp, 0.0)
         T = np.where(w < 0.0, p.sigma_c + kp * w,
                      np.where(w < p.delta_c, p.sigma_c * (1.0 - w / p.delta_c), 0.0))
         dT = np.where(w < 0.0, kp, np.where(w < p.delta_c, -p.sigma_c / p.delta_c, 0.0))
@@ -712,24 +719,55 @@ class Oracle:
 
     def accept_step(self):
         """End of step: beta = 1 where alpha = 1 and the opening exceeds
-        delta_f at a quadrature point; w^n <- w^{n+1}; t += dt; rescale."""
+        delta_f at a quadrature point; w^n <- w^{n+1}; t += dt; rescale.
+        With prm.beta_connected such a facet takes fluid only when it shares
+        a node with a fluid-filled facet (one wetted in this step counts), so
+        a dry crack not reached by the fluid stays dry."""
         new = 0
+        cand = []
         for f in np.nonzero(self.m.face_crackable)[0]:
             if self.alpha[f] and not self.beta[f]:
                 w = self.face_kinematics(f, self.U)[-1]
                 if w.max() > self.prm.delta_f:
-                    self.beta[f] = 1
-                    new += 1
+                    cand.append(int(f))
+        if not self.prm.beta_connected:
+            for f in cand:
+                self.beta[f] = 1
+                new += 1
+        else:
+            wet = set()
+            for f in np.nonzero(self.beta)[0]:
+                wet.update(self.face_nodes(int(f)))
+            grew = True
+            while grew:
+                grew = False
+                for f in cand:
+                    if not self.beta[f] and wet.intersection(self.face_nodes(f)):
+                        self.beta[f] = 1
+                        wet.update(self.face_nodes(f))
+                        new += 1
+                        grew = True
         self.w_old = self.opening_at_face_nodes(self.U)
         self.t += self.prm.dt
         self.update_scaling()
         return new
 
-    def set_state(self, U, P, alpha, beta, w_old=None, t=0.0):
+    def face_nodes(self, f):
+        """Global node ids of facet f (its minus side's face nodes)."""
+        e = self.m.face_elems[f, 0]
+        loc = face_local_nodes(self.dim, int(self.m.face_local[f, 0]))
+        return set(int(g) for g in self.m.elem_nodes[e, loc])
+
+    def set_state(self, U, P, alpha, beta, w_old=None, t=0.0, spent=None):
+        """spent: facets of a pre-existing dry crack (cohesive law spent;
+        they must have alpha = 1), zeros when not given."""
         self.U = np.array(U, dtype=np.float64)
         self.P = np.array(P, dtype=np.float64)
         self.alpha = np.array(alpha, dtype=np.int8)
         self.beta = np.array(beta, dtype=np.int8)
+        self.spent = np.zeros(self.nf, dtype=np.int8) if spent is None else np.array(spent, dtype=np.int8)
+        if np.any(self.spent & (self.alpha == 0)):
+            raise ValueError("a spent facet must have alpha = 1")
         self.w_old = self.opening_at_face_nodes(self.U) if w_old is None else \
             np.array(w_old, dtype=np.float64).reshape(self.nf, self.nfn)
         self.t = float(t)
