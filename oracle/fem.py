@@ -22,6 +22,10 @@ Serebrinsky, Radovitzky, arXiv 1911.10275), written as directly as possible:
 * Activation: alpha from the DG traction exceeding sigma_c at any facet
   quadrature point (Sec. 3, activation of the TSL); beta at the end of the
   step from the opening exceeding delta_f (Remark in Sec. 3).
+* Pre-existing dry crack (Sec. 4.5), as an option: facets whose cohesive
+  law is spent (no strength in opening, contact penalty in closure) and,
+  with Params.beta_connected, fluid entering a failed facet only from a
+  fluid-filled neighbour.
 
 Readings where the paper is silent are named in the docstrings below.
 Quadrature rules come from library routines (numpy Gauss-Legendre, scipy
