@@ -248,10 +248,14 @@ hf_status hf_get_stats(const hf_mesh* h, int64_t* st);
 
 const char* hf_last_error(const hf_mesh* h);
 
-/* Failure detection without a fault.  The preconditioner waits on mbarriers
- * for its bulk copies with a bounded number of polls (default 2^22); a wait
- * that runs out raises a device flag, the kernel goes on, and the solve
- * returns HF_ERR_TIMEOUT with the context intact.  hf_set_wait_limit sets
+/* Failure detection without a fault.  The ILU(0) apply and the streamed
+ * Gram-Schmidt kernels wait on mbarriers for their bulk copies with a
+ * bounded number of polls (default 2^22); a wait that runs out raises a
+ * device flag holding the first site that gave up (1 ILU(0) apply; 2-4 the
+ * Gram-Schmidt dot kernel's producer, u/w and consumer waits; 5-6 the update
+ * kernel's producer and consumer waits; 7 the drain at kernel exit; 8 the
+ * self-test below), the kernel goes on, and the solve returns HF_ERR_TIMEOUT
+ * with the context intact and the site in hf_last_error.  hf_set_wait_limit sets
  * that bound (1..2^30 polls).  hf_check_wait_timeout runs the same bounded
  * wait on a barrier that nothing ever completes (no copies issued) and
  * returns HF_ERR_TIMEOUT once it has given up (HF_OK would mean the wait
